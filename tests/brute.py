@@ -1,0 +1,152 @@
+"""Brute-force evaluation of the paper's set definitions with Python sets.
+
+Used by the tests to pin the C oracle on tiny inputs (N <= ~48): every set is
+built by enumerating all ranks, nodes and stored entries, exactly as the
+equations of Secs. 2, 2.1, 4.1 and 4.2 of Bienz, Gropp, Olson (arXiv 1612.08060)
+state them, with the same readings of the open points as the oracle (listed in the
+oracle's header).  Nothing here is fast or clever on purpose.
+"""
+from __future__ import annotations
+
+
+def partition(n, n_p):
+    """R(r) as explicit sets; the first n mod n_p ranks get one more row."""
+    q, rem = divmod(n, n_p)
+    R, start = [], 0
+    for r in range(n_p):
+        size = q + (1 if r < rem else 0)
+        R.append(set(range(start, start + size)))
+        start += size
+    return R
+
+
+def brute_plan(n, rows, n_p, ppn, map_text=False):
+    """rows[i] = set of stored columns of row i.  Returns a dict of dicts:
+    STD/J0/J1/J2/INTER: {(src, dst): sorted tuple}; NODE: {(n, m): tuple};
+    BLL/BNL/LBUF: {rank: tuple}; T, U: {rank: set of nodes}; G: {rank: set};
+    split: list of (on_process, on_node, off_node) counts per row."""
+    R = partition(n, n_p)
+    nn = (n_p + ppn - 1) // ppn
+    node_ranks = [[r for r in range(n_p) if r // ppn == x] for x in range(nn)]
+    node_rows = [set().union(*(R[r] for r in node_ranks[x])) for x in range(nn)]
+    A = {(i, j) for i in range(n) for j in rows[i]}
+
+    def uses(I_rows, J_cols):
+        return {(i, j) for (i, j) in A if i in I_rows and j in J_cols}
+
+    out = {}
+    # Eqs. P and D
+    STD = {}
+    for r in range(n_p):
+        for t in range(n_p):
+            if r == t:
+                continue
+            D = {j for (i, j) in uses(R[t], R[r])}
+            if D:
+                STD[(r, t)] = tuple(sorted(D))
+    out["STD"] = STD
+    # Eqs. N and E
+    NODE = {}
+    for a in range(nn):
+        for b in range(nn):
+            if a == b:
+                continue
+            E = {j for (i, j) in uses(node_rows[b], node_rows[a])}
+            if E:
+                NODE[(a, b)] = tuple(sorted(E))
+    out["NODE"] = NODE
+    # T and U: the mapping rule (largest |E| first on the sending side; on the
+    # receiving side ascending |E| from the last process, as the tables show)
+    T = {r: set() for r in range(n_p)}
+    U = {r: set() for r in range(n_p)}
+    for a in range(nn):
+        P = len(node_ranks[a])
+        sends = sorted([m for (x, m) in NODE if x == a], key=lambda m: (-len(NODE[(a, m)]), m))
+        for k, m in enumerate(sends):
+            T[node_ranks[a][k % P]].add(m)
+        recvs = [x for (x, m) in NODE if m == a]
+        if map_text:
+            recvs.sort(key=lambda x: (-len(NODE[(x, a)]), x))
+        else:
+            recvs.sort(key=lambda x: (len(NODE[(x, a)]), x))
+        for k, x in enumerate(recvs):
+            U[node_ranks[a][P - 1 - (k % P)]].add(x)
+    out["T"], out["U"] = T, U
+    # Eq. G and Eq. I
+    G = {r: set() for r in range(n_p)}
+    INTER = {}
+    for r in range(n_p):
+        for q in range(n_p):
+            m, x = q // ppn, r // ppn
+            if m in T[r] and x in U[q]:
+                G[r].add(q)
+                INTER[(r, q)] = NODE[(x, m)]
+    out["G"], out["INTER"] = G, INTER
+    # Eq. IL0: on_node -> off_node
+    J0 = {}
+    for s in range(n_p):
+        sent = set()
+        for q in G[s]:
+            sent |= set(INTER[(s, q)])
+        for p in node_ranks[s // ppn]:
+            if p == s:
+                continue
+            J = {j for j in sent if j in R[p]}
+            if J:
+                J0[(p, s)] = tuple(sorted(J))
+    out["J0"] = J0
+    # Eq. IL1: off_node -> on_node
+    J1 = {}
+    for q in range(n_p):
+        recv = set()
+        for (r, d), idx in INTER.items():
+            if d == q:
+                recv |= set(idx)
+        for s in node_ranks[q // ppn]:
+            if s == q:
+                continue
+            J = {j for (i, j) in A if i in R[s] and j in recv}
+            if J:
+                J1[(q, s)] = tuple(sorted(J))
+    out["J1"] = J1
+    # Eq. IL2: on_node -> on_node
+    J2 = {}
+    for p in range(n_p):
+        for s in node_ranks[p // ppn]:
+            if s == p:
+                continue
+            J = {j for (i, j) in uses(R[s], R[p])}
+            if J:
+                J2[(p, s)] = tuple(sorted(J))
+    out["J2"] = J2
+    # receive layouts of each rank and the aggregator buffers
+    BLL, BNL, LBUF = {}, {}, {}
+    for t in range(n_p):
+        own_node = node_rows[t // ppn]
+        on = {j for (i, j) in A if i in R[t] and j in own_node and j not in R[t]}
+        off = {j for (i, j) in A if i in R[t] and j not in own_node}
+        if on:
+            BLL[t] = tuple(sorted(on))
+        if off:
+            BNL[t] = tuple(sorted(off))
+        lb = set()
+        for (p, s), idx in J0.items():
+            if s == t:
+                lb |= set(idx)
+        if lb:
+            LBUF[t] = tuple(sorted(lb))
+    out["BLL"], out["BNL"], out["LBUF"] = BLL, BNL, LBUF
+    split = []
+    for i in range(n):
+        t = next(r for r in range(n_p) if i in R[r])
+        c = [0, 0, 0]
+        for j in rows[i]:
+            if j in R[t]:
+                c[0] += 1
+            elif j in node_rows[t // ppn]:
+                c[1] += 1
+            else:
+                c[2] += 1
+        split.append(tuple(c))
+    out["split"] = split
+    return out

@@ -1,0 +1,93 @@
+"""The CPU oracle's plans against a literal Python evaluation of the set
+definitions (tests/brute.py) on tiny random patterns, for many (n_p, ppn),
+including uneven partitions and a partial last node; and its products against
+dense numpy products."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from brute import brute_plan
+from paper_1612_08060_gb300.inputs import random_pattern
+
+LISTS = [("STD", O.STD), ("NODE", O.NODE), ("INTER", O.INTER), ("J0", O.J0), ("J1", O.J1),
+         ("J2", O.J2)]
+LAYOUTS = [("BLL", O.BLL), ("BNL", O.BNL), ("LBUF", O.LBUF)]
+
+CASES = []
+for seed, (n, dens) in enumerate([(7, 0.3), (12, 0.25), (17, 0.2), (24, 0.15), (31, 0.1),
+                                   (40, 0.08), (48, 0.3)]):
+    for n_p, ppn in [(1, 1), (2, 1), (3, 2), (5, 2), (6, 3), (7, 4), (n, 1), (n, 4),
+                     (min(n, 9), 9), (min(n, 11), 3), (min(n, 16), 5)]:
+        if n_p <= n:
+            CASES.append((n, dens, seed, n_p, ppn))
+
+
+def _rows(A):
+    return [set(A.col[A.row_ptr[i]:A.row_ptr[i + 1]].tolist()) for i in range(A.n)]
+
+
+@pytest.mark.parametrize("n,dens,seed,n_p,ppn", CASES)
+def test_plans_match_set_definitions(n, dens, seed, n_p, ppn):
+    A = random_pattern(n, dens, seed)
+    plan = O.OraclePlan(A.row_ptr, A.col, n_p, ppn)
+    b = brute_plan(n, _rows(A), n_p, ppn)
+    for name, kind in LISTS:
+        assert plan.list_dict(kind) == b[name], name
+    for name, kind in LAYOUTS:
+        got = {s: idx for (s, d), idx in plan.list_dict(kind).items()}
+        assert all(s == d for (s, d) in plan.list_dict(kind))
+        assert got == b[name], name
+    assert [tuple(r) for r in plan.split().tolist()] == b["split"]
+
+
+@pytest.mark.parametrize("n_p,ppn", [(6, 2), (9, 4), (12, 5)])
+def test_map_text_rule(n_p, ppn):
+    A = random_pattern(36, 0.12, 77)
+    plan = O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=O.MAP_TEXT)
+    b = brute_plan(36, _rows(A), n_p, ppn, map_text=True)
+    assert plan.list_dict(O.INTER) == b["INTER"]
+    assert plan.list_dict(O.J0) == b["J0"]
+    assert plan.list_dict(O.J1) == b["J1"]
+
+
+@pytest.mark.parametrize("n,dens,seed,n_p,ppn", CASES[::3])
+def test_napspmv_and_spmv_equal_dense(n, dens, seed, n_p, ppn):
+    A = random_pattern(n, dens, seed)
+    v = np.random.default_rng(seed + 100).uniform(-1, 1, n)
+    ref = A.to_dense() @ v
+    scale = np.abs(A.to_dense()) @ np.abs(v)
+    w1 = O.spmv(A.row_ptr, A.col, A.val, v)
+    plan = O.OraclePlan(A.row_ptr, A.col, n_p, ppn)
+    w2 = plan.napspmv(A.row_ptr, A.col, A.val, v)
+    tol = 4 * np.finfo(float).eps * scale + 1e-300
+    assert np.all(np.abs(w1 - ref) <= tol)
+    assert np.all(np.abs(w2 - ref) <= tol)
+
+
+def test_invariants_random():
+    """E(n,m) is the union of D(r,t) over r on n, t on m; one inter-node message
+    per node pair; node-aware inter-node counts never exceed the standard ones;
+    every intra-node message stays on its node; nobody sends to itself."""
+    for seed, (n, n_p, ppn) in enumerate([(40, 10, 3), (48, 16, 4), (45, 9, 2), (30, 30, 7)]):
+        A = random_pattern(n, 0.15, 300 + seed)
+        plan = O.OraclePlan(A.row_ptr, A.col, n_p, ppn)
+        D = plan.list_dict(O.STD)
+        E = plan.list_dict(O.NODE)
+        U = {}
+        for (r, t), idx in D.items():
+            if r // ppn != t // ppn:
+                U.setdefault((r // ppn, t // ppn), set()).update(idx)
+        assert {k: tuple(sorted(v)) for k, v in U.items()} == E
+        inter = plan.list_dict(O.INTER)
+        assert len(inter) == len(E)
+        assert sorted(inter.values()) == sorted(E.values())
+        s = plan.stats()
+        assert s["nap_inter_msgs"] <= s["std_inter_msgs"]
+        assert s["nap_inter_vals"] <= s["std_inter_vals"]
+        for kind in (O.J0, O.J1, O.J2):
+            for (a, b) in plan.list_dict(kind):
+                assert a != b and a // ppn == b // ppn
+        for (a, b) in itertools.chain(D, inter):
+            assert a != b
