@@ -1,0 +1,340 @@
+"""Benchmark of the node-aware SpMV apply on one GB300 (or N replicas).
+
+Workload (default): 3D 7-point Poisson 128^3 (N = 2,097,152, nnz = 14,581,760),
+FP64 CSR, n_p = 1024 simulated processes, ppn = 16 (64 simulated nodes); one step
+= 100 chained applies x <- (1/12) A x in one persistent launch (the fused
+engine).  Metric: algorithmic GB/s of the apply (plain-SpMV stream plus every
+value moved by the node-aware message steps), as a fraction of measured HBM
+bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (the path is
+simulated on one GPU and has no exchange between GPUs): value = all replicas'
+bytes / max-over-ranks time.  ``--impl reference`` times the CPU oracle (plain
+FP64 CSR SpMV) on the host cores instead, one apply per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NAPSpMV GB/s (% of HBM peak); served p50/p99 vs plain loop at stated rel err"
+SCALE = 1.0 / 12.0  # keeps the 7-point chain O(1): max row sum of |A| is 12
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("apply.cu", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1612_08060_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "fused_apply_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d.get("traffic_bytes_per_launch")
+
+
+def build_workload(cfg):
+    from paper_1612_08060_gb300 import inputs
+    w = inputs.workload(cfg)
+    A = w.build()
+    v = inputs.vector(A.n, w.seed)
+    return w, A, v
+
+
+def run_reference(args):
+    """The CPU oracle on the host cores: one plain FP64 CSR SpMV per step."""
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    import oracle
+    from paper_1612_08060_gb300 import inputs  # noqa: F401
+    w, A, v = build_workload(args.config)
+    t0 = time.perf_counter()
+    op = oracle.OraclePlan(A.row_ptr, A.col, w.n_p, w.ppn)
+    plan_s = time.perf_counter() - t0
+    st = op.stats()
+    B = bytes_per_apply(A, st)
+    for _ in range(args.warmup):
+        oracle.spmv(A.row_ptr, A.col, A.val, v)
+    t0 = time.perf_counter()
+    x = v
+    for _ in range(args.steps):
+        x = oracle.spmv(A.row_ptr, A.col, A.val, v)
+    el = time.perf_counter() - t0
+    val = B * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GB/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": A.n, "nnz": A.nnz, "n_p": w.n_p, "ppn": w.ppn,
+                   "applies_per_step": 1},
+        "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} plain FP64 CSR SpMVs of the full matrix, "
+                                   "single thread, same byte count as the GPU apply",
+                         "plan_build_s": round(plan_s, 3)},
+        "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    del x
+    print(json.dumps(line), flush=True)
+
+
+def bytes_per_apply(A, st):
+    n, nnz = A.n, A.nnz
+    b_csr = 4.0 * (n + 1) + nnz * 12.0 + 16.0 * n
+    b_msg = 20.0 * (st["bll_total"] + st["lbuf_total"] + 2 * st["nap_inter_vals"] +
+                    st["bnl_total"])
+    return b_csr + b_msg
+
+
+def cpu_baseline_leg(A, v, w_gpu_one, B, budget_s):
+    """The oracle timed on this host's cores on a bounded sample, and the
+    relative error of one GPU apply against it."""
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.spmv(A.row_ptr, A.col, A.val, v)
+    one = time.perf_counter() - t0
+    reps = max(1, int(budget_s / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.spmv(A.row_ptr, A.col, A.val, v)
+    el = time.perf_counter() - t0
+    rel = float(np.linalg.norm(w_gpu_one - ref) / np.linalg.norm(ref))
+    return {"value": round(B * reps / el / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} plain FP64 CSR SpMVs of the full matrix (single thread, "
+                      f"{el:.1f} s), bytes counted as for the GPU apply",
+            "gpu_vs_oracle_relerr": rel}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=100, help="chained applies per step")
+    ap.add_argument("--engine", default="fused", choices=["fused", "phased"])
+    ap.add_argument("--vec", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import __graft_entry__
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    __graft_entry__.build()
+    from paper_1612_08060_gb300 import napspmv as nap
+
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    w, A, v = build_workload(args.config)
+    t0 = time.perf_counter()
+    plan = nap.napspmv_plan(A.row_ptr, A.col, A.val, w.n_p, w.ppn, nap.F32_VALUES)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    st = nap.napspmv_plan_stats(plan)
+    B = bytes_per_apply(A, st)
+    B_csr = st["bytes_csr_f64"]
+    assert abs(B - (st["bytes_csr_f64"] + st["bytes_msg"])) < 1.0
+    opts = nap.make_opts(engine=nap.ENGINE_FUSED if args.engine == "fused" else nap.ENGINE_PHASED,
+                         vec=args.vec, chunk=args.chunk, tile_rows=args.tile_rows,
+                         ctas_per_sm=args.ctas_per_sm)
+    eff = nap.napspmv_get_default_opts(plan)
+    stream = torch.cuda.Stream(device=dev)
+    vd = torch.from_numpy(v).to(dev)
+    wd = torch.empty_like(vd)
+
+    def step():
+        nap.napspmv_apply_ex(plan, vd, wd, args.reps, SCALE, opts, stream=stream)
+
+    with torch.cuda.stream(stream):
+        # one plain apply for the parity figure of the CPU leg
+        nap.napspmv_apply_ex(plan, vd, wd, 1, 1.0, opts, stream=stream)
+        assert nap.napspmv_status(plan, stream) == 0
+        w_one = wd.cpu().numpy()
+        for _ in range(args.warmup):
+            step()
+        assert nap.napspmv_status(plan, stream) == 0
+        sampler = ClockSampler(dev.index)
+        if not args.no_clocks:
+            sampler.start()
+            time.sleep(0.3)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        launches0 = nap.napspmv_launch_count()
+        ev[0].record(stream)
+        for i in range(args.steps):
+            step()
+            ev[i + 1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize(dev)
+        launches = nap.napspmv_launch_count() - launches0
+        if ws > 1:
+            torch.distributed.barrier()
+        clocks = sampler.stop() if not args.no_clocks else None
+        rc = nap.napspmv_status(plan, stream)
+        assert rc == 0, rc
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * B * args.reps * args.steps / (total_ms * 1e-3) / 1e9
+    avg_launch = statistics.mean(per)
+    achieved = B * args.reps / (avg_launch * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+
+    # end to end through the host-buffer entry point (copies in the timed region)
+    e2e_steps = max(3, min(args.steps, 50))
+    vh = torch.from_numpy(v.copy()).pin_memory()
+    wh = torch.empty_like(vh).pin_memory()
+    nap.napspmv_apply_host(plan, vh, wh, args.reps, SCALE, stream=stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        nap.napspmv_apply_host(plan, vh, wh, args.reps, SCALE, stream=stream)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": round(ws * B * args.reps * e2e_steps / e2e_s / 1e9, 3), "unit": "GB/s",
+           "h2d_bytes_per_step": int(vh.numel() * 8), "d2h_bytes_per_step": int(wh.numel() * 8)}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n": A.n, "nnz": A.nnz, "n_p": w.n_p, "ppn": w.ppn,
+                   "applies_per_step": args.reps, "scale": SCALE, "engine": args.engine,
+                   "vec": opts.vec or eff.vec, "chunk": opts.chunk or eff.chunk,
+                   "tile_rows": opts.tile_rows or eff.tile_rows,
+                   "l2": "inputs larger than L2: each apply streams the 175 MB col/val "
+                         "arrays (L2 129 MB); not flushed between steps",
+                   "parallelism": f"replicas{ws}"},
+        "bytes_per_apply": {"total": B, "csr": B_csr, "msg": st["bytes_msg"]},
+        "csr_gbs": round(B_csr * args.reps / (avg_launch * 1e-3) / 1e9, 3),
+        "gflops": round(2.0 * A.nnz * args.reps / (avg_launch * 1e-3) / 1e9, 3),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_kind": peak_kind, "traffic": ncu_traffic(),
+                     "kernel": "k_fused (one launch = 100 chained applies)"},
+        "gpu_launches": int(launches),
+        "plan": {"gpu_plan_ms": round(plan_ms, 2), "std_msgs": st["std_msgs"],
+                 "std_inter_msgs": st["std_inter_msgs"], "std_inter_vals": st["std_inter_vals"],
+                 "nap_inter_msgs": st["nap_inter_msgs"], "nap_inter_vals": st["nap_inter_vals"],
+                 "nap_intra_msgs": st["nap_intra_msgs"], "nap_intra_vals": st["nap_intra_vals"]},
+        "e2e": e2e,
+        "clocks": clocks,
+    }
+    if not args.no_cpu and ws == 1:
+        line["cpu_baseline"] = cpu_baseline_leg(A, v, w_one, B, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * napspmv.h -- C ABI of the GB300 node-aware parallel SpMV library.
+ *
+ * The library computes w <- A v (Sec. 1 of Bienz, Gropp, Olson, "Node aware
+ * sparse matrix-vector multiplication", arXiv 1612.08060) the way the paper's
+ * node-aware algorithm NAPSpMV (Sec. 4, Algorithm "NAPSpMV") does, with every
+ * simulated process and node living on one GPU:
+ *
+ *   - the rows of the N x N matrix A are split into n_p contiguous blocks, one
+ *     per simulated process (Sec. 2, Eq. R), and the processes are grouped ppn
+ *     per simulated node, process r being (r mod ppn, floor(r / ppn));
+ *   - each process's rows are split into on-process, on-node and off-node
+ *     column blocks (Sec. 2, Eqs. on_proc, on_node, off_node);
+ *   - napspmv_plan builds, on the GPU, the standard communication plan
+ *     (Sec. 2.1, Eqs. P, D) and the node-aware plan (Sec. 4.1, Eqs. N, E, T,
+ *     U, G, I; Sec. 4.2, Eqs. L0/IL0, L1_send/IL1, L2/IL2), and the three-block
+ *     CSR with each block's columns pointing into that block's receive buffer;
+ *   - napspmv_apply runs, on the GPU, every message of the node-aware
+ *     algorithm as a device gather or copy in HBM (on_node -> on_node and
+ *     on_node -> off_node local exchanges, packing of g_send, the inter-node
+ *     transfer g_send -> g_recv, the off_node -> on_node forwarding) and the
+ *     three-block SpMV, for all simulated processes in one persistent launch.
+ *
+ * Conventions for every call:
+ *   - Return value: NAPSPMV_OK (0) or a negative NAPSPMV_ERR_* code; the
+ *     message of the last error of the calling thread is napspmv_last_error().
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is queued on it asynchronously unless stated otherwise.
+ *   - Vectors are FP64, N entries, contiguous.  Device pointers must be device
+ *     memory of the plan's device (the device current at napspmv_plan).
+ *   - A plan owns all its device memory.  It is not thread-safe: calls on one
+ *     plan (or one workspace) must not overlap on the host, and applies that
+ *     use the same workspace must be ordered on one stream.
+ *   - Limits: N < 2^30, nnz < 2^31, and every receive buffer < 2^30 values.
+ *     Larger inputs are rejected with NAPSPMV_ERR_UNSUPPORTED.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one fails with NAPSPMV_ERR_CUDA.
+ */
+#ifndef NAPSPMV_H
+#define NAPSPMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ return codes */
+#define NAPSPMV_OK 0
+#define NAPSPMV_ERR_ARG (-1)         /* invalid argument or malformed CSR        */
+#define NAPSPMV_ERR_OOM (-2)         /* device or host allocation failed         */
+#define NAPSPMV_ERR_CUDA (-3)        /* a CUDA runtime call failed               */
+#define NAPSPMV_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up       */
+#define NAPSPMV_ERR_STATE (-5)       /* call not valid in the object's state     */
+#define NAPSPMV_ERR_UNSUPPORTED (-6) /* size beyond the limits above             */
+
+/* ------------------------------------------------------------ memory kinds */
+#define NAPSPMV_HOST 0
+#define NAPSPMV_DEVICE 1
+
+/* -------------------------------------------------------------- plan flags */
+/* Keep an FP32 copy of A's values for NAPSPMV_PREC_F32 applies. */
+#define NAPSPMV_F32_VALUES (1u << 0)
+/* Map the receiving side of every node pair by |E(n,m)| descending, as the
+ * prose after Eq. U states, instead of the default that reproduces the
+ * paper's Tables U and G (ascending |E|, last process first). */
+#define NAPSPMV_MAP_TEXT (1u << 1)
+
+/* ------------------------------------------------------------- apply modes */
+#define NAPSPMV_PREC_F64 0 /* FP64 values, FP64 products and sums            */
+#define NAPSPMV_PREC_F32 1 /* FP32-stored values, FP32 products, FP64 sums   */
+
+#define NAPSPMV_ENGINE_FUSED 0  /* one persistent launch for all phases     */
+#define NAPSPMV_ENGINE_PHASED 1 /* one kernel per phase (control variant)   */
+
+typedef struct napspmv_plan_s napspmv_plan_t;
+typedef struct napspmv_ws_s napspmv_ws_t;
+
+/* A CSR matrix.  row_ptr[0] = 0, row_ptr non-decreasing, row_ptr[n] = nnz,
+ * 0 <= col[k] < n, no (i, j) stored twice.  Every stored entry counts as a
+ * nonzero, zero values included (the paper's "A_ij != 0" is read as
+ * structural).  `mem` says whether the three arrays are host or device
+ * memory; they are only read during napspmv_plan and may be freed after. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const double *val;
+    int32_t mem; /* NAPSPMV_HOST or NAPSPMV_DEVICE */
+} napspmv_csr;
+
+/* Launch options of an apply.  Zero fields take the plan's defaults (which
+ * napspmv_set_default_opts, e.g. from an autotuner, may change). */
+typedef struct {
+    int32_t precision;   /* NAPSPMV_PREC_F64 or NAPSPMV_PREC_F32               */
+    int32_t engine;      /* NAPSPMV_ENGINE_FUSED or NAPSPMV_ENGINE_PHASED      */
+    int32_t vec;         /* lanes per matrix row: 1, 2, 4, 8, 16 or 32         */
+    int32_t ctas_per_sm; /* persistent CTAs per SM (fused engine)              */
+    int32_t chunk;       /* gather elements per work item (fused engine)       */
+    int32_t tile_rows;   /* matrix rows per work item (fused engine)           */
+    int32_t timeout_ms;  /* limit of every device-side wait                    */
+    int32_t debug_stall; /* test hook: 1 makes the first work item wait on a
+                            counter nothing increments, so the launch ends
+                            with NAPSPMV_ERR_TIMEOUT after timeout_ms          */
+} napspmv_opts;
+
+/* Communication statistics of a plan.  Counts are numbers of messages and
+ * of vector values; "max ... proc" is the maximum over sending processes (the
+ * per-process figures the paper plots in Sec. 5).  Standard plan: the messages
+ * of Eqs. P, D.  Node-aware plan: inter-node = the messages of Eq. I, one per
+ * node pair; intra-node = J0 + J1 + J2 (Eqs. IL0, IL1, IL2), each step
+ * counted on its own. */
+typedef struct {
+    int64_t std_msgs, std_vals, std_intra_msgs, std_intra_vals;
+    int64_t std_inter_msgs, std_inter_vals;
+    int64_t std_max_inter_msgs_proc, std_max_inter_vals_proc;
+    int64_t std_max_intra_msgs_proc, std_max_intra_vals_proc;
+    int64_t std_max_msg_vals;
+    int64_t nap_inter_msgs, nap_inter_vals;
+    int64_t j0_msgs, j0_vals, j1_msgs, j1_vals, j2_msgs, j2_vals;
+    int64_t nap_intra_msgs, nap_intra_vals;
+    int64_t nap_max_inter_msgs_proc, nap_max_inter_vals_proc;
+    int64_t nap_max_intra_msgs_proc, nap_max_intra_vals_proc;
+    int64_t nap_max_inter_msg_vals;
+    int64_t node_pairs, bll_total, bnl_total, lbuf_total;
+    int64_t nnz_on_process, nnz_on_node, nnz_off_node;
+    /* Algorithmic bytes of one apply: the plain-SpMV stream
+     * 4(N+1) + nnz (4 + s_val) + 8N (v) + 8N (w), and the message part: every
+     * value moved by a gather (J2, J0, pack, unpack) costs 8 B read + 8 B
+     * write + 4 B index, every value of the transfer g_send -> g_recv 8 + 8 + 4
+     * (its destination index). */
+    double bytes_csr_f64, bytes_csr_f32, bytes_msg;
+    double plan_ms; /* wall time of napspmv_plan on the host clock */
+} napspmv_stats;
+
+/* Build the plans of A for n_p simulated processes, ppn per node.
+ *   A      CSR (host or device memory), see napspmv_csr.
+ *   n_p    1 <= n_p <= N;  ppn >= 1 (the last node may hold fewer processes).
+ *   flags  NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT.
+ *   out    receives the plan; the caller frees it with napspmv_plan_destroy.
+ * Runs on the current device and synchronises it.  Errors: ERR_ARG for a
+ * malformed CSR or bad n_p / ppn, ERR_UNSUPPORTED beyond the size limits,
+ * ERR_OOM, ERR_CUDA.  Paper: Secs. 2, 2.1, 4.1, 4.2 (all plan equations). */
+int napspmv_plan(const napspmv_csr *A, int32_t n_p, int32_t ppn, uint32_t flags,
+                 napspmv_plan_t **out);
+
+/* w <- A v with the plan's default options (FP64).  v, w: device, N values,
+ * must not overlap.  Asynchronous on `stream`.  Device-side failures (a wait
+ * that timed out) are sticky and reported by napspmv_status.
+ * Paper: Algorithm NAPSpMV (Sec. 4) with local_comm (Sec. 4.2). */
+int napspmv_apply(napspmv_plan_t *P, const double *v, double *w, void *stream);
+
+/* reps chained applies in one launch: x_0 = v, x_{k+1} = scale * A x_k, and
+ * w <- x_reps.  v is not modified; the plan's workspace holds the
+ * intermediate vector.  reps >= 1. */
+int napspmv_apply_n(napspmv_plan_t *P, const double *v, double *w, int32_t reps, double scale,
+                    void *stream);
+
+/* As napspmv_apply_n with explicit options (NULL = defaults) and workspace
+ * (NULL = the plan's own).  A workspace holds the receive buffers and the
+ * dependency counters of one in-flight apply. */
+int napspmv_apply_ex(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w,
+                     int32_t reps, double scale, const napspmv_opts *opts, void *stream);
+
+/* End-to-end variant on HOST vectors (pageable or pinned): copies v in,
+ * runs reps chained applies, copies w out and synchronises `stream`.
+ * Returns the device-side status like napspmv_status. */
+int napspmv_apply_host(napspmv_plan_t *P, const double *v_host, double *w_host, int32_t reps,
+                       double scale, void *stream);
+
+/* One persistent launch over `count` independent applies (each with its own
+ * plan, workspace, vectors, reps and scale): the batched form used by the
+ * request server.  ws[i] may be NULL only if no other entry uses the same
+ * plan's own workspace.  count <= 64.  Fused engine only. */
+int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const *ws,
+                        const double *const *v, double *const *w, const int32_t *reps,
+                        const double *scale, const napspmv_opts *opts, void *stream);
+
+/* Synchronise `stream`, return and clear the plan's device-side status
+ * (NAPSPMV_OK or NAPSPMV_ERR_TIMEOUT) of its own workspace. */
+int napspmv_status(napspmv_plan_t *P, void *stream);
+int napspmv_ws_status(napspmv_ws_t *ws, void *stream);
+
+/* Extra workspaces for concurrent applies of one plan. */
+int napspmv_ws_create(napspmv_plan_t *P, napspmv_ws_t **out);
+void napspmv_ws_destroy(napspmv_ws_t *ws);
+
+/* Statistics of the plan (host copy; no device work). */
+int napspmv_plan_stats(const napspmv_plan_t *P, napspmv_stats *out);
+
+/* Canonical plan arrays for comparison with an independent implementation.
+ * which: NAPSPMV_LIST_* below.  buf: host int64 array of *count entries; with
+ * buf == NULL, *count receives the required length.  Message lists are laid
+ * out as [m, total, src[m], dst[m], ptr[m+1], idx[total]] with messages in
+ * ascending (src, dst) and idx ascending within a message; src / dst are
+ * processes (nodes for NAPSPMV_LIST_NODE).  BLL / BNL / LBUF hold one
+ * "message" per process with a non-empty buffer, src = dst = process, idx
+ * the global columns in buffer order.  NAPSPMV_LIST_TU is [m, send_proc[m],
+ * recv_proc[m]]: the local process on the sending and receiving node that
+ * carries node pair k of the NODE list.  NAPSPMV_LIST_SPLIT is [n, then 3
+ * counts per row: on_process, on_node, off_node].  Synchronous. */
+#define NAPSPMV_LIST_STD 0   /* P(r), D(r,t)               Eqs. P, D        */
+#define NAPSPMV_LIST_NODE 1  /* N(n), E(n,m)               Eqs. N, E        */
+#define NAPSPMV_LIST_INTER 2 /* G, I((p,n),(q,m))          Eqs. G, I        */
+#define NAPSPMV_LIST_J0 3    /* on_node -> off_node        Eqs. L0, IL0     */
+#define NAPSPMV_LIST_J1 4    /* off_node -> on_node        Eqs. L1, IL1     */
+#define NAPSPMV_LIST_J2 5    /* on_node -> on_node         Eqs. L2, IL2     */
+#define NAPSPMV_LIST_BLL 6   /* on-node receive buffer b_{l->l} per process */
+#define NAPSPMV_LIST_BNL 7   /* off-node receive buffer b_{nl->l}           */
+#define NAPSPMV_LIST_LBUF 8  /* aggregator buffer b_{l->nl}                 */
+#define NAPSPMV_LIST_TU 9    /* T, U assignment            Eqs. T, U        */
+#define NAPSPMV_LIST_SPLIT 10
+int napspmv_plan_export(const napspmv_plan_t *P, int32_t which, int64_t *buf, int64_t *count);
+
+/* Default options of the plan (used where a napspmv_opts field is 0). */
+int napspmv_get_default_opts(const napspmv_plan_t *P, napspmv_opts *out);
+int napspmv_set_default_opts(napspmv_plan_t *P, const napspmv_opts *opts);
+
+/* Conjugate gradients with iterative refinement for SPD A.
+ * Outer loop in FP64: r = b - A x with the FP64 apply, stop when
+ * ||r|| / ||b|| <= rtol; otherwise solve A d = r approximately by CG whose
+ * applies use the FP32-stored values (NAPSPMV_PREC_F32; the plan needs
+ * NAPSPMV_F32_VALUES) with FP64 vectors and FP64 dot products, to relative
+ * residual inner_rtol or inner_max iterations, then x += d.
+ *   b, x   device, N values; x holds the initial guess on entry.
+ *   info   optional: iterations and final relative residual.
+ * Synchronous (polls the residual on the host every few iterations).
+ * Errors: ERR_ARG, ERR_STATE (plan without FP32 values), ERR_TIMEOUT. */
+typedef struct {
+    int32_t outer_iters;
+    int32_t inner_iters; /* total over all outer iterations */
+    double relres;       /* ||b - A x|| / ||b||, FP64 */
+    int32_t converged;
+} napspmv_cg_info;
+int napspmv_cg_ir(napspmv_plan_t *P, const double *b, double *x, double rtol, double inner_rtol,
+                  int32_t max_outer, int32_t inner_max, napspmv_cg_info *info, void *stream);
+
+/* Plain FP64 CG (no refinement), same conventions; for comparison. */
+int napspmv_cg(napspmv_plan_t *P, const double *b, double *x, double rtol, int32_t max_it,
+               napspmv_cg_info *info, void *stream);
+
+/* Deterministic FP64 dot product of two device vectors of length n (fixed
+ * partition and summation order, so the result does not depend on timing).
+ * result: device pointer to one double.  Asynchronous. */
+int napspmv_dot(const double *x, const double *y, int64_t n, double *result, void *stream);
+
+void napspmv_plan_destroy(napspmv_plan_t *P);
+const char *napspmv_strerror(int code);
+const char *napspmv_last_error(void);
+/* Number of kernel launches this thread queued through the library so far
+ * (for the benchmark's launch count). */
+int64_t napspmv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NAPSPMV_H */

@@ -1,0 +1,137 @@
+// internal.h -- data structures shared by the library's translation units.
+//
+// A plan holds the three-block CSR, the index arrays of every message step of
+// the node-aware algorithm and the work-item list of the fused persistent
+// kernel; a workspace holds the receive buffers and dependency counters of one
+// in-flight apply.  Nothing here is part of the C ABI (include/napspmv.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/napspmv.h"
+
+namespace nap {
+
+// ------------------------------------------------------------------ errors
+void set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *what);
+void count_launch(int64_t n = 1);
+
+#define NAP_CUDA(call)                                            \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ::nap::cuda_error(e_, #call); \
+    } while (0)
+
+// ----------------------------------------------------------- column coding
+// A column of the three-block CSR stores its block in the top two bits:
+// 0 = on-process (index into v), 1 = on-node (index into b_{l->l}),
+// 2 = off-node (index into b_{nl->l}); the low 30 bits are the index.
+constexpr uint32_t kBlockShift = 30;
+constexpr uint32_t kIndexMask = (1u << 30) - 1;
+// A pack source with the top bit set reads the aggregator buffer b_{l->nl},
+// otherwise v.
+constexpr uint32_t kFromLbuf = 0x80000000u;
+
+// --------------------------------------------------------- fused work items
+enum ItemKind : int32_t {
+    kGatherJ2 = 0,  // b_{l->l}[k]  = v[bll_j[k]]          (on_node -> on_node)
+    kGatherJ0 = 1,  // b_{l->nl}[k] = v[lbuf_j[k]]         (on_node -> off_node)
+    kPack = 2,      // g_send[k] = v or b_{l->nl} (pack_src[k])
+    kTransfer = 3,  // g_recv[xfer_dst[k]] = g_send[k]     (inter-node)
+    kUnpack = 4,    // b_{nl->l}[k] = g_recv[unp_src[k]]   (off_node -> on_node)
+    kSpmv = 5,      // rows [b, e) of the three-block SpMV
+};
+// Dependency counters per node, in this order, then the arrival counter.
+enum Counter : int32_t { kC1 = 0, kC2 = 1, kC3 = 2, kC4 = 3, kC5 = 4, kArr = 5, kNumCounters = 6 };
+
+struct Item {
+    int32_t kind;
+    int32_t node;  // node whose data the item touches (sender node for kTransfer)
+    int32_t b, e;  // element (or row) range
+    int32_t msg;   // kTransfer: first g_send message overlapping [b, e)
+    int32_t pad[3];
+};
+
+struct ItemSet {
+    int32_t chunk = 0, tile_rows = 0;
+    int32_t n_items = 0;
+    Item *d_items = nullptr;
+    // per-apply increments of every counter, [kNumCounters][nn]
+    uint64_t *d_cnt = nullptr;
+};
+
+// --------------------------------------------------------------- plan lists
+struct HostList {
+    int64_t m = 0, total = 0;
+    std::vector<int32_t> src, dst;
+    std::vector<int64_t> ptr;
+    int32_t *d_idx = nullptr;  // global column indices, device
+};
+
+enum ListKind { L_STD = 0, L_NODE, L_INTER, L_J0, L_J1, L_J2, L_BLL, L_BNL, L_LBUF, L_COUNT };
+
+}  // namespace nap
+
+struct napspmv_ws_s {
+    napspmv_plan_t *plan = nullptr;
+    int device = 0;
+    double *bll = nullptr, *lbuf = nullptr, *gsend = nullptr, *grecv = nullptr, *bnl = nullptr;
+    double *xtmp = nullptr;            // chained-apply intermediate vector
+    double *hv = nullptr, *hw = nullptr;  // staging of napspmv_apply_host
+    unsigned long long *ctr = nullptr;  // ticket + kNumCounters * nn
+    int *err = nullptr;                 // sticky device status
+    bool owned_by_plan = false;
+};
+
+struct napspmv_plan_s {
+    int device = 0;
+    int64_t n = 0, nnz = 0;
+    int32_t np = 0, ppn = 0, nn = 0;
+    uint32_t flags = 0;
+    int num_sms = 0;
+
+    nap::HostList lists[nap::L_COUNT];
+    std::vector<int32_t> send_proc, recv_proc;  // per NODE pair
+    int32_t *d_split = nullptr;                 // 3 per row
+
+    // three-block CSR
+    int32_t *d_rowptr = nullptr;
+    uint32_t *d_colenc = nullptr;
+    double *d_val = nullptr;
+    float *d_val32 = nullptr;
+
+    // sizes of the buffers and index arrays of the message steps
+    int64_t n_bll = 0, n_lbuf = 0, n_gs = 0, n_bnl = 0;
+    uint32_t *d_pack_src = nullptr;  // [n_gs]
+    int32_t *d_xfer_dst = nullptr;   // [n_gs]
+    int32_t *d_unp_src = nullptr;    // [n_bnl]
+    // BLL / LBUF list idx arrays double as the J2 / J0 gather sources.
+
+    // per-node ranges (host) used to cut work items
+    std::vector<int64_t> node_bll, node_lbuf, node_gs, node_bnl, node_rows;  // [nn+1]
+    std::vector<int64_t> gs_msg_off;       // [n_inter + 1] g_send offsets in INTER order
+    std::vector<int32_t> gs_msg_dstnode;   // [n_inter]
+    int32_t *d_gs_msg_off = nullptr;       // device copies
+    int32_t *d_gs_msg_dstnode = nullptr;
+
+    nap::ItemSet items;
+    napspmv_opts defaults{};
+    napspmv_stats stats{};
+    napspmv_ws_t *ws = nullptr;  // the plan's own workspace
+};
+
+namespace nap {
+int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows);
+int ws_alloc(napspmv_plan_t *P, napspmv_ws_t *ws);
+void ws_free(napspmv_ws_t *ws);
+void plan_free(napspmv_plan_t *P);
+napspmv_opts resolve_opts(const napspmv_plan_t *P, const napspmv_opts *o);
+int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const *ws,
+                const double *const *v, double *const *w, const int32_t *reps,
+                const double *scale, const napspmv_opts *opts, cudaStream_t s);
+}  // namespace nap

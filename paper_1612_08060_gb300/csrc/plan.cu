@@ -1,0 +1,943 @@
+// plan.cu -- GPU construction of the standard and node-aware communication
+// plans and of the three-block CSR.
+//
+// Every set of the paper is obtained on the device as a sorted, de-duplicated
+// array of packed 64-bit keys:
+//   (r, t, j)  r = owner(j) sends column j to the row owner t   Eqs. P, D
+//   (n, m, j)  node n sends column j to node m                  Eqs. N, E
+//   (t, j)     receive layouts of rank t                        (b_{l->l}, b_{nl->l})
+//   (p, s, j)  on_node -> off_node                              Eqs. L0, IL0
+//   (q, s, j)  off_node -> on_node                              Eqs. L1, IL1
+// built with CUB radix sort / select / run-length encode (library primitives
+// for plan time only; the apply path is hand-written).  The per-node-pair
+// process assignment T/U (Eqs. T, U and the mapping rule after them) is
+// O(node pairs) and runs on the host.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace nap {
+namespace {
+
+struct NapError {
+    int code;
+    std::string msg;
+};
+
+inline void ck(cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw NapError{e == cudaErrorMemoryAllocation ? NAPSPMV_ERR_OOM : NAPSPMV_ERR_CUDA,
+                       std::string(what) + ": " + cudaGetErrorString(e)};
+    }
+}
+#define CK(x) ck((x), #x)
+
+template <class T>
+struct dvec {
+    T *p = nullptr;
+    int64_t n = 0;
+    dvec() = default;
+    explicit dvec(int64_t count) { alloc(count); }
+    void alloc(int64_t count)
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = count;
+        if (count > 0) CK(cudaMalloc(&p, sizeof(T) * (size_t)count));
+    }
+    ~dvec()
+    {
+        if (p) cudaFree(p);
+    }
+    T *release()
+    {
+        T *q = p;
+        p = nullptr;
+        return q;
+    }
+    dvec(const dvec &) = delete;
+    dvec &operator=(const dvec &) = delete;
+};
+
+template <class T>
+T *upload(const std::vector<T> &h)
+{
+    T *d = nullptr;
+    size_t bytes = sizeof(T) * std::max<size_t>(h.size(), 1);
+    CK(cudaMalloc(&d, bytes));
+    if (!h.empty()) CK(cudaMemcpy(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    return d;
+}
+
+constexpr uint64_t SENT = ~0ull;
+
+inline int bits_for(int64_t maxval)  // bits to hold 0..maxval
+{
+    int b = 1;
+    while (b < 63 && (int64_t(1) << b) <= maxval) b++;
+    return b;
+}
+
+struct Part {  // row partition of Eq. R, first N mod n_p ranks one row longer
+    int64_t q, rem, big;
+    __host__ __device__ int64_t owner(int64_t j) const
+    {
+        return j < big ? j / (q + 1) : rem + (j - big) / q;
+    }
+    __host__ __device__ int64_t start(int64_t r) const { return r * q + (r < rem ? r : rem); }
+};
+
+inline int blocks_for(int64_t n, int t = 256)
+{
+    int64_t b = (n + t - 1) / t;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
+}
+
+// ----------------------------------------------------------------- kernels
+
+__global__ void k_check_rowptr(const int64_t *rp, int64_t n, int64_t nnz, int *bad)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (rp[i + 1] < rp[i]) atomicOr(bad, 1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicOr(bad, 1);
+}
+
+__global__ void k_row_of(const int64_t *rp, int64_t n, const int32_t *col, int32_t *row_of,
+                         int *bad)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+            row_of[k] = (int32_t)i;
+            int32_t c = col[k];
+            if (c < 0 || c >= n) atomicOr(bad, 2);
+        }
+    }
+}
+
+__global__ void k_pair_keys(const int32_t *row_of, const int32_t *col, int64_t nnz, int jb,
+                            uint64_t *keys)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x)
+        keys[k] = ((uint64_t)row_of[k] << jb) | (uint32_t)col[k];
+}
+
+__global__ void k_adjacent_equal(const uint64_t *keys, int64_t n, int *bad)
+{
+    for (int64_t k = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        if (keys[k] == keys[k - 1]) atomicOr(bad, 4);
+}
+
+// Block of every stored entry (Eqs. on_proc, on_node, off_node) and the
+// (r, t, j) key of every off-process entry.
+__global__ void k_classify(const int32_t *row_of, const int32_t *col, int64_t nnz, Part part,
+                           int32_t ppn, int rb, int jb, uint8_t *tag, uint64_t *key,
+                           unsigned long long *blk_count)
+{
+    unsigned long long c[3] = {0, 0, 0};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = row_of[k], j = col[k];
+        int64_t t = part.owner(i), r = part.owner(j);
+        uint8_t b = (r == t) ? 0 : ((r / ppn == t / ppn) ? 1 : 2);
+        tag[k] = b;
+        c[b]++;
+        key[k] = b ? (((uint64_t)r << (rb + jb)) | ((uint64_t)t << jb) | (uint64_t)j) : SENT;
+    }
+    for (int q = 0; q < 3; q++) {
+        unsigned long long s = c[q];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0 && s) atomicAdd(&blk_count[q], s);
+    }
+}
+
+__global__ void k_shift(const uint64_t *in, int64_t n, int sh, uint64_t *out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = in[k] >> sh;
+}
+
+__global__ void k_low(const uint64_t *in, int64_t n, uint64_t mask, int32_t *out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = (int32_t)(in[k] & mask);
+}
+
+// (r, t, j) -> (t, j)
+__global__ void k_rekey_tj(const uint64_t *in, int64_t n, int rb, int jb, uint64_t *out)
+{
+    uint64_t rmask = (1ull << rb) - 1, jmask = (1ull << jb) - 1;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t t = (in[k] >> jb) & rmask;
+        out[k] = (t << jb) | (in[k] & jmask);
+    }
+}
+
+// (r, t, j) -> (node r, node t, j)
+__global__ void k_rekey_node(const uint64_t *in, int64_t n, int rb, int jb, int nb, int32_t ppn,
+                             uint64_t *out)
+{
+    uint64_t rmask = (1ull << rb) - 1, jmask = (1ull << jb) - 1;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t r = in[k] >> (rb + jb), t = (in[k] >> jb) & rmask;
+        out[k] = ((r / ppn) << (nb + jb)) | ((t / ppn) << jb) | (in[k] & jmask);
+    }
+}
+
+struct NotSent {
+    __host__ __device__ bool operator()(uint64_t k) const { return k != SENT; }
+};
+struct SameNode {
+    int rb, jb, ppn;
+    bool want;
+    __host__ __device__ bool operator()(uint64_t k) const
+    {
+        uint64_t r = k >> (rb + jb), t = (k >> jb) & ((1ull << rb) - 1);
+        return ((r / ppn) == (t / ppn)) == want;
+    }
+};
+
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, int32_t x)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Content of g_send (INTER messages in (src, dst) order), its transfer
+// destinations in g_recv, the message of every element and the J0 keys.
+__global__ void k_fill_gsend(int64_t n_gs, const int64_t *gs_off, int64_t n_msg,
+                             const int32_t *msg_pair, const int32_t *msg_src,
+                             const int64_t *pair_gr_off, const int32_t *node_ptr,
+                             const int32_t *node_idx, Part part, int rb, int jb, int32_t *gs_j,
+                             int32_t *xfer_dst, int32_t *msg_of, uint64_t *j0key)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_gs;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = n_msg - 1;  // last message with gs_off <= e
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (gs_off[mid] <= e)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        int32_t k = msg_pair[lo];
+        int64_t off = e - gs_off[lo];
+        int32_t j = node_idx[node_ptr[k] + off];
+        gs_j[e] = j;
+        xfer_dst[e] = (int32_t)(pair_gr_off[k] + off);
+        msg_of[e] = (int32_t)lo;
+        int64_t s = msg_src[lo], p = part.owner(j);
+        j0key[e] = (p != s) ? (((uint64_t)p << (rb + jb)) | ((uint64_t)s << jb) | (uint64_t)j)
+                            : SENT;
+    }
+}
+
+__global__ void k_pack_src(int64_t n_gs, const int32_t *gs_j, const int32_t *msg_of,
+                           const int32_t *msg_src, const int32_t *lbuf_ptr, const int32_t *lbuf_j,
+                           Part part, uint32_t *pack_src, int *bad)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_gs;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t j = gs_j[e], s = msg_src[msg_of[e]];
+        if (part.owner(j) == s) {
+            pack_src[e] = (uint32_t)j;
+        } else {
+            int64_t b = lbuf_ptr[s], len = lbuf_ptr[s + 1] - b;
+            int64_t pos = lower_bound_i32(lbuf_j + b, len, j);
+            if (pos >= len || lbuf_j[b + pos] != j) atomicOr(bad, 8);
+            pack_src[e] = kFromLbuf | (uint32_t)(b + pos);
+        }
+    }
+}
+
+// Off-node receive entries (t, j): the receiving process q of j's node pair,
+// the J1 key (q, t, j) when q != t, and the g_recv position to unpack from.
+__global__ void k_unpack_src(int64_t n_bnl, const uint64_t *bnl_keys, int jb, Part part,
+                             int32_t ppn, int nb, int64_t n_pairs, const uint64_t *pair_key,
+                             const int32_t *recv_proc, const int64_t *pair_gr_off,
+                             const int32_t *node_ptr, const int32_t *node_idx, int rb,
+                             uint64_t *j1key, int32_t *unp_src, int *bad)
+{
+    uint64_t jmask = (1ull << jb) - 1;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_bnl;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t t = bnl_keys[e] >> jb;
+        int32_t j = (int32_t)(bnl_keys[e] & jmask);
+        uint64_t nj = part.owner(j) / ppn, m = t / ppn;
+        uint64_t pk = (nj << nb) | m;
+        int64_t lo = 0, hi = n_pairs;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (pair_key[mid] < pk)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        if (lo >= n_pairs || pair_key[lo] != pk) {
+            atomicOr(bad, 16);
+            unp_src[e] = 0;
+            j1key[e] = SENT;
+            continue;
+        }
+        int64_t q = (int64_t)m * ppn + recv_proc[lo];
+        j1key[e] = ((int64_t)t != q) ? (((uint64_t)q << (rb + jb)) | (t << jb) | (uint64_t)j)
+                                     : SENT;
+        int64_t b = node_ptr[lo], len = node_ptr[lo + 1] - b;
+        int64_t pos = lower_bound_i32(node_idx + b, len, j);
+        if (pos >= len || node_idx[b + pos] != j) atomicOr(bad, 16);
+        unp_src[e] = (int32_t)(pair_gr_off[lo] + pos);
+    }
+}
+
+// Three-block CSR: every row's entries reordered on_process | on_node |
+// off_node (stored order kept inside a block), columns coded by block.
+__global__ void k_three_block(const int64_t *rp, int64_t n, const int32_t *col, const double *val,
+                              const uint8_t *tag, Part part, const int32_t *bll_ptr,
+                              const int32_t *bll_j, const int32_t *bnl_ptr, const int32_t *bnl_j,
+                              uint32_t *colenc, double *val_out, float *val32_out,
+                              int32_t *split, int32_t *rowptr32, int *bad)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t t = part.owner(i);
+        int64_t pos = rp[i];
+        rowptr32[i] = (int32_t)rp[i];
+        if (i == n - 1) rowptr32[n] = (int32_t)rp[n];
+        for (int blk = 0; blk < 3; blk++) {
+            int32_t cnt = 0;
+            for (int64_t k = rp[i]; k < rp[i + 1]; k++) {
+                if (tag[k] != blk) continue;
+                int32_t j = col[k];
+                uint32_t enc;
+                if (blk == 0) {
+                    enc = (uint32_t)j;
+                } else {
+                    const int32_t *ptr = blk == 1 ? bll_ptr : bnl_ptr;
+                    const int32_t *arr = blk == 1 ? bll_j : bnl_j;
+                    int64_t b = ptr[t], len = ptr[t + 1] - b;
+                    int64_t p = lower_bound_i32(arr + b, len, j);
+                    if (p >= len || arr[b + p] != j) atomicOr(bad, 32);
+                    enc = ((uint32_t)blk << kBlockShift) | (uint32_t)(b + p);
+                }
+                colenc[pos] = enc;
+                val_out[pos] = val[k];
+                if (val32_out) val32_out[pos] = (float)val[k];
+                pos++;
+                cnt++;
+            }
+            split[3 * i + blk] = cnt;
+        }
+    }
+}
+
+// ------------------------------------------------------------ CUB helpers
+
+struct Cub {
+    cudaStream_t st = 0;
+    dvec<char> tmp;
+    dvec<int> num;
+    Cub() : num(1) {}
+    void *temp(size_t bytes)
+    {
+        if ((int64_t)bytes > tmp.n) tmp.alloc((int64_t)bytes + 256);
+        return tmp.p;
+    }
+    int64_t read_num()
+    {
+        int h = 0;
+        CK(cudaMemcpy(&h, num.p, sizeof(int), cudaMemcpyDeviceToHost));
+        return h;
+    }
+    template <class F>
+    int64_t select(const uint64_t *in, int64_t n, uint64_t *out, F f)
+    {
+        if (n == 0) return 0;
+        size_t b = 0;
+        CK(cub::DeviceSelect::If(nullptr, b, in, out, num.p, (int)n, f, st));
+        CK(cub::DeviceSelect::If(temp(b), b, in, out, num.p, (int)n, f, st));
+        return read_num();
+    }
+    // sorts keys[0..n) ascending over bits [0, end_bit); alt is scratch
+    void sort(uint64_t *keys, uint64_t *alt, int64_t n, int end_bit)
+    {
+        if (n <= 1) return;
+        cub::DoubleBuffer<uint64_t> db(keys, alt);
+        size_t b = 0;
+        CK(cub::DeviceRadixSort::SortKeys(nullptr, b, db, (int)n, 0, end_bit, st));
+        CK(cub::DeviceRadixSort::SortKeys(temp(b), b, db, (int)n, 0, end_bit, st));
+        if (db.Current() != keys)
+            CK(cudaMemcpyAsync(keys, db.Current(), sizeof(uint64_t) * n,
+                               cudaMemcpyDeviceToDevice, st));
+    }
+    int64_t unique(const uint64_t *in, int64_t n, uint64_t *out)
+    {
+        if (n == 0) return 0;
+        size_t b = 0;
+        CK(cub::DeviceSelect::Unique(nullptr, b, in, out, num.p, (int)n, st));
+        CK(cub::DeviceSelect::Unique(temp(b), b, in, out, num.p, (int)n, st));
+        return read_num();
+    }
+    // runs of equal keys: unique values and lengths, copied to the host
+    void rle(const uint64_t *in, int64_t n, std::vector<uint64_t> &uniq,
+             std::vector<int32_t> &len)
+    {
+        uniq.clear();
+        len.clear();
+        if (n == 0) return;
+        dvec<uint64_t> u(n);
+        dvec<int32_t> c(n);
+        size_t b = 0;
+        CK(cub::DeviceRunLengthEncode::Encode(nullptr, b, in, u.p, c.p, num.p, (int)n, st));
+        CK(cub::DeviceRunLengthEncode::Encode(temp(b), b, in, u.p, c.p, num.p, (int)n, st));
+        int64_t m = read_num();
+        uniq.resize(m);
+        len.resize(m);
+        CK(cudaMemcpy(uniq.data(), u.p, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(len.data(), c.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
+    }
+};
+
+// A sorted, unique key array (prefix << jb | j) becomes a message list whose
+// prefix is (src << fb | dst); with fb < 0 the prefix is one process id used
+// as both src and dst (the per-process buffer layouts).
+void make_list(Cub &cb, const uint64_t *keys, int64_t cnt, int fb, int jb, HostList &L)
+{
+    L = HostList();
+    L.ptr.assign(1, 0);
+    if (cnt == 0) return;
+    dvec<uint64_t> pre(cnt);
+    k_shift<<<blocks_for(cnt), 256, 0, cb.st>>>(keys, cnt, jb, pre.p);
+    CK(cudaGetLastError());
+    std::vector<uint64_t> u;
+    std::vector<int32_t> len;
+    cb.rle(pre.p, cnt, u, len);
+    L.m = (int64_t)u.size();
+    L.total = cnt;
+    L.src.resize(L.m);
+    L.dst.resize(L.m);
+    L.ptr.resize(L.m + 1);
+    L.ptr[0] = 0;
+    for (int64_t k = 0; k < L.m; k++) {
+        if (fb < 0) {
+            L.src[k] = L.dst[k] = (int32_t)u[k];
+        } else {
+            L.src[k] = (int32_t)(u[k] >> fb);
+            L.dst[k] = (int32_t)(u[k] & ((1ull << fb) - 1));
+        }
+        L.ptr[k + 1] = L.ptr[k] + len[k];
+    }
+    CK(cudaMalloc(&L.d_idx, sizeof(int32_t) * cnt));
+    k_low<<<blocks_for(cnt), 256, 0, cb.st>>>(keys, cnt, (1ull << jb) - 1, L.d_idx);
+    CK(cudaGetLastError());
+}
+
+// Per-process offsets [np+1] of a per-process layout list (empty ranks too).
+std::vector<int32_t> full_ptr(const HostList &L, int32_t np)
+{
+    std::vector<int32_t> p(np + 1, 0);
+    std::vector<int64_t> cnt(np, 0);
+    for (int64_t k = 0; k < L.m; k++) cnt[L.src[k]] = L.ptr[k + 1] - L.ptr[k];
+    for (int32_t r = 0; r < np; r++) p[r + 1] = (int32_t)(p[r] + cnt[r]);
+    return p;
+}
+
+int check_bad(const dvec<int> &bad, const char *what)
+{
+    int h = 0;
+    CK(cudaMemcpy(&h, bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) throw NapError{NAPSPMV_ERR_ARG, std::string(what)};
+    return 0;
+}
+
+void host_stats(napspmv_plan_t *P)
+{
+    napspmv_stats &S = P->stats;
+    int64_t np = P->np, ppn = P->ppn;
+    std::vector<int64_t> a(4 * np, 0), b(4 * np, 0);
+    const HostList &St = P->lists[L_STD];
+    for (int64_t k = 0; k < St.m; k++) {
+        int64_t len = St.ptr[k + 1] - St.ptr[k];
+        bool inter = (St.src[k] / ppn) != (St.dst[k] / ppn);
+        S.std_msgs++;
+        S.std_vals += len;
+        if (inter) {
+            S.std_inter_msgs++;
+            S.std_inter_vals += len;
+            a[4 * St.src[k] + 0]++;
+            a[4 * St.src[k] + 1] += len;
+        } else {
+            S.std_intra_msgs++;
+            S.std_intra_vals += len;
+            a[4 * St.src[k] + 2]++;
+            a[4 * St.src[k] + 3] += len;
+        }
+        S.std_max_msg_vals = std::max(S.std_max_msg_vals, len);
+    }
+    const HostList &In = P->lists[L_INTER];
+    for (int64_t k = 0; k < In.m; k++) {
+        int64_t len = In.ptr[k + 1] - In.ptr[k];
+        S.nap_inter_msgs++;
+        S.nap_inter_vals += len;
+        S.nap_max_inter_msg_vals = std::max(S.nap_max_inter_msg_vals, len);
+        b[4 * In.src[k] + 0]++;
+        b[4 * In.src[k] + 1] += len;
+    }
+    int64_t *jm[3] = {&S.j0_msgs, &S.j1_msgs, &S.j2_msgs};
+    int64_t *jv[3] = {&S.j0_vals, &S.j1_vals, &S.j2_vals};
+    const int lk[3] = {L_J0, L_J1, L_J2};
+    for (int q = 0; q < 3; q++) {
+        const HostList &J = P->lists[lk[q]];
+        for (int64_t k = 0; k < J.m; k++) {
+            int64_t len = J.ptr[k + 1] - J.ptr[k];
+            (*jm[q])++;
+            (*jv[q]) += len;
+            b[4 * J.src[k] + 2]++;
+            b[4 * J.src[k] + 3] += len;
+        }
+    }
+    S.nap_intra_msgs = S.j0_msgs + S.j1_msgs + S.j2_msgs;
+    S.nap_intra_vals = S.j0_vals + S.j1_vals + S.j2_vals;
+    for (int64_t r = 0; r < np; r++) {
+        S.std_max_inter_msgs_proc = std::max(S.std_max_inter_msgs_proc, a[4 * r + 0]);
+        S.std_max_inter_vals_proc = std::max(S.std_max_inter_vals_proc, a[4 * r + 1]);
+        S.std_max_intra_msgs_proc = std::max(S.std_max_intra_msgs_proc, a[4 * r + 2]);
+        S.std_max_intra_vals_proc = std::max(S.std_max_intra_vals_proc, a[4 * r + 3]);
+        S.nap_max_inter_msgs_proc = std::max(S.nap_max_inter_msgs_proc, b[4 * r + 0]);
+        S.nap_max_inter_vals_proc = std::max(S.nap_max_inter_vals_proc, b[4 * r + 1]);
+        S.nap_max_intra_msgs_proc = std::max(S.nap_max_intra_msgs_proc, b[4 * r + 2]);
+        S.nap_max_intra_vals_proc = std::max(S.nap_max_intra_vals_proc, b[4 * r + 3]);
+    }
+    S.node_pairs = P->lists[L_NODE].m;
+    S.bll_total = P->n_bll;
+    S.bnl_total = P->n_bnl;
+    S.lbuf_total = P->n_lbuf;
+    double N = (double)P->n, nnz = (double)P->nnz;
+    S.bytes_csr_f64 = 4.0 * (N + 1) + nnz * 12.0 + 16.0 * N;
+    S.bytes_csr_f32 = 4.0 * (N + 1) + nnz * 8.0 + 16.0 * N;
+    S.bytes_msg = 20.0 * (double)(P->n_bll + P->n_lbuf + P->n_gs + P->n_bnl) + 20.0 * (double)P->n_gs;
+}
+
+void build(napspmv_plan_t *P, const napspmv_csr *A)
+{
+    const int64_t n = A->n, nnz = A->nnz;
+    const int32_t np = P->np, ppn = P->ppn, nn = P->nn;
+    Cub cb;
+    Part part{n / np, n % np, (n % np) * (n / np + 1)};
+    const int jb = bits_for(n - 1), rb = bits_for(np - 1), nb = bits_for(nn - 1);
+    if (2 * rb + jb > 63)
+        throw NapError{NAPSPMV_ERR_UNSUPPORTED, "N and n_p too large for 64-bit plan keys"};
+
+    // ---- upload and validate the CSR
+    dvec<int64_t> rp(n + 1);
+    dvec<int32_t> col(nnz);
+    dvec<double> val(nnz);
+    CK(cudaMemcpy(rp.p, A->row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDefault));
+    if (nnz) {
+        CK(cudaMemcpy(col.p, A->col, sizeof(int32_t) * nnz, cudaMemcpyDefault));
+        CK(cudaMemcpy(val.p, A->val, sizeof(double) * nnz, cudaMemcpyDefault));
+    }
+    dvec<int> bad(1);
+    CK(cudaMemset(bad.p, 0, sizeof(int)));
+    k_check_rowptr<<<blocks_for(n), 256>>>(rp.p, n, nnz, bad.p);
+    CK(cudaGetLastError());
+    check_bad(bad, "row_ptr must start at 0, never decrease and end at nnz");
+    dvec<int32_t> row_of(nnz);
+    k_row_of<<<blocks_for(n), 256>>>(rp.p, n, col.p, row_of.p, bad.p);
+    CK(cudaGetLastError());
+    check_bad(bad, "column index out of range [0, n)");
+
+    dvec<uint64_t> keys(nnz), alt(nnz);
+    if (nnz) {
+        k_pair_keys<<<blocks_for(nnz), 256>>>(row_of.p, col.p, nnz, jb, keys.p);
+        CK(cudaGetLastError());
+        cb.sort(keys.p, alt.p, nnz, 2 * jb);
+        k_adjacent_equal<<<blocks_for(nnz), 256>>>(keys.p, nnz, bad.p);
+        CK(cudaGetLastError());
+        check_bad(bad, "an entry (i, j) is stored twice");
+    }
+
+    // ---- classify; the standard plan (Eqs. P, D)
+    dvec<uint8_t> tag(nnz);
+    dvec<unsigned long long> blk(3);
+    CK(cudaMemset(blk.p, 0, 3 * sizeof(unsigned long long)));
+    if (nnz) {
+        k_classify<<<blocks_for(nnz), 256>>>(row_of.p, col.p, nnz, part, ppn, rb, jb, tag.p,
+                                             keys.p, blk.p);
+        CK(cudaGetLastError());
+    }
+    unsigned long long hb[3];
+    CK(cudaMemcpy(hb, blk.p, sizeof(hb), cudaMemcpyDeviceToHost));
+    P->stats.nnz_on_process = (int64_t)hb[0];
+    P->stats.nnz_on_node = (int64_t)hb[1];
+    P->stats.nnz_off_node = (int64_t)hb[2];
+    row_of.alloc(0);
+
+    int64_t c = cb.select(keys.p, nnz, alt.p, NotSent{});
+    cb.sort(alt.p, keys.p, c, 2 * rb + jb);
+    dvec<uint64_t> std_u(c);
+    int64_t U = cb.unique(alt.p, c, std_u.p);
+    make_list(cb, std_u.p, U, rb, jb, P->lists[L_STD]);
+
+    // on-node part: J2 (Eqs. L2, IL2) and b_{l->l}; off-node part: E, b_{nl->l}
+    dvec<uint64_t> on_u(U), off_u(U);
+    int64_t n_on = cb.select(std_u.p, U, on_u.p, SameNode{rb, jb, ppn, true});
+    int64_t n_off = cb.select(std_u.p, U, off_u.p, SameNode{rb, jb, ppn, false});
+    std_u.alloc(0);
+    make_list(cb, on_u.p, n_on, rb, jb, P->lists[L_J2]);
+
+    dvec<uint64_t> tj(std::max(n_on, n_off)), tj_alt(std::max(n_on, n_off));
+    if (n_on) {
+        k_rekey_tj<<<blocks_for(n_on), 256>>>(on_u.p, n_on, rb, jb, tj.p);
+        CK(cudaGetLastError());
+    }
+    cb.sort(tj.p, tj_alt.p, n_on, rb + jb);
+    make_list(cb, tj.p, n_on, -1, jb, P->lists[L_BLL]);
+    on_u.alloc(0);
+
+    if (n_off) {
+        k_rekey_tj<<<blocks_for(n_off), 256>>>(off_u.p, n_off, rb, jb, tj.p);
+        CK(cudaGetLastError());
+    }
+    cb.sort(tj.p, tj_alt.p, n_off, rb + jb);
+    dvec<uint64_t> bnl_keys(n_off);
+    if (n_off)
+        CK(cudaMemcpy(bnl_keys.p, tj.p, sizeof(uint64_t) * n_off, cudaMemcpyDeviceToDevice));
+    make_list(cb, tj.p, n_off, -1, jb, P->lists[L_BNL]);
+
+    // node plan (Eqs. N, E)
+    if (n_off) {
+        k_rekey_node<<<blocks_for(n_off), 256>>>(off_u.p, n_off, rb, jb, nb, ppn, tj.p);
+        CK(cudaGetLastError());
+    }
+    cb.sort(tj.p, tj_alt.p, n_off, 2 * nb + jb);
+    dvec<uint64_t> node_u(n_off);
+    int64_t n_node = cb.unique(tj.p, n_off, node_u.p);
+    make_list(cb, node_u.p, n_node, nb, jb, P->lists[L_NODE]);
+    off_u.alloc(0);
+    tj.alloc(0);
+    tj_alt.alloc(0);
+
+    P->n_bll = P->lists[L_BLL].total;
+    P->n_bnl = P->lists[L_BNL].total;
+    if (P->n_bll >= (1ll << 30) || P->n_bnl >= (1ll << 30))
+        throw NapError{NAPSPMV_ERR_UNSUPPORTED, "receive buffer beyond 2^30 values"};
+
+    // ---- T, U (host; O(node pairs))
+    const HostList &ND = P->lists[L_NODE];
+    const int64_t M = ND.m;
+    P->send_proc.assign(M, 0);
+    P->recv_proc.assign(M, 0);
+    {
+        auto procs = [&](int64_t node) { return (int64_t)std::min<int64_t>(ppn, np - node * ppn); };
+        std::vector<std::vector<int64_t>> out_of(nn), in_of(nn);
+        for (int64_t k = 0; k < M; k++) {
+            out_of[ND.src[k]].push_back(k);
+            in_of[ND.dst[k]].push_back(k);
+        }
+        auto len = [&](int64_t k) { return ND.ptr[k + 1] - ND.ptr[k]; };
+        for (int64_t x = 0; x < nn; x++) {
+            auto &o = out_of[x];
+            std::stable_sort(o.begin(), o.end(), [&](int64_t a, int64_t b) {
+                if (len(a) != len(b)) return len(a) > len(b);
+                return ND.dst[a] < ND.dst[b];
+            });
+            for (size_t k = 0; k < o.size(); k++) P->send_proc[o[k]] = (int32_t)(k % procs(x));
+            auto &i = in_of[x];
+            bool text = (P->flags & NAPSPMV_MAP_TEXT) != 0;
+            std::stable_sort(i.begin(), i.end(), [&](int64_t a, int64_t b) {
+                if (len(a) != len(b)) return text ? len(a) > len(b) : len(a) < len(b);
+                return ND.src[a] < ND.src[b];
+            });
+            for (size_t k = 0; k < i.size(); k++)
+                P->recv_proc[i[k]] = (int32_t)(procs(x) - 1 - (int64_t)(k % procs(x)));
+        }
+    }
+
+    // ---- G, I: one message per node pair, in (src, dst) order for g_send and
+    // (dst, src) order for g_recv
+    std::vector<int32_t> psrc(M), pdst(M);
+    for (int64_t k = 0; k < M; k++) {
+        psrc[k] = ND.src[k] * ppn + P->send_proc[k];
+        pdst[k] = ND.dst[k] * ppn + P->recv_proc[k];
+    }
+    std::vector<int32_t> sorder(M), rorder(M);
+    std::iota(sorder.begin(), sorder.end(), 0);
+    std::iota(rorder.begin(), rorder.end(), 0);
+    std::sort(sorder.begin(), sorder.end(), [&](int32_t a, int32_t b) {
+        return psrc[a] != psrc[b] ? psrc[a] < psrc[b] : pdst[a] < pdst[b];
+    });
+    std::sort(rorder.begin(), rorder.end(), [&](int32_t a, int32_t b) {
+        return pdst[a] != pdst[b] ? pdst[a] < pdst[b] : psrc[a] < psrc[b];
+    });
+    std::vector<int64_t> gs_off(M + 1, 0), pair_gr_off(M, 0);
+    std::vector<int32_t> msg_src(M), msg_dstnode(M);
+    for (int64_t i = 0; i < M; i++) {
+        int32_t k = sorder[i];
+        gs_off[i + 1] = gs_off[i] + (ND.ptr[k + 1] - ND.ptr[k]);
+        msg_src[i] = psrc[k];
+        msg_dstnode[i] = ND.dst[k];
+    }
+    {
+        int64_t o = 0;
+        for (int64_t i = 0; i < M; i++) {
+            int32_t k = rorder[i];
+            pair_gr_off[k] = o;
+            o += ND.ptr[k + 1] - ND.ptr[k];
+        }
+    }
+    P->n_gs = gs_off[M];
+    if (P->n_gs >= (1ll << 30))
+        throw NapError{NAPSPMV_ERR_UNSUPPORTED, "g_send beyond 2^30 values"};
+    {
+        HostList &In = P->lists[L_INTER];
+        In = HostList();
+        In.m = M;
+        In.total = P->n_gs;
+        In.src.resize(M);
+        In.dst.resize(M);
+        In.ptr = gs_off;
+        for (int64_t i = 0; i < M; i++) {
+            In.src[i] = psrc[sorder[i]];
+            In.dst[i] = pdst[sorder[i]];
+        }
+    }
+    std::vector<int32_t> node_ptr32(M + 1);
+    for (int64_t k = 0; k <= M; k++) node_ptr32[k] = (int32_t)ND.ptr[k];
+    dvec<int64_t> d_gs_off;
+    d_gs_off.p = upload(gs_off);
+    dvec<int32_t> d_msg_pair, d_msg_src, d_node_ptr;
+    d_msg_pair.p = upload(sorder);
+    d_msg_src.p = upload(msg_src);
+    d_node_ptr.p = upload(node_ptr32);
+    dvec<int64_t> d_pair_gr_off;
+    d_pair_gr_off.p = upload(pair_gr_off);
+
+    const int64_t ngs = P->n_gs;
+    dvec<int32_t> msg_of(ngs);
+    dvec<uint64_t> j0key(ngs), j0alt(ngs);
+    if (ngs) {
+        CK(cudaMalloc(&P->lists[L_INTER].d_idx, sizeof(int32_t) * ngs));
+        CK(cudaMalloc(&P->d_xfer_dst, sizeof(int32_t) * ngs));
+        k_fill_gsend<<<blocks_for(ngs), 256>>>(ngs, d_gs_off.p, M, d_msg_pair.p, d_msg_src.p,
+                                              d_pair_gr_off.p, d_node_ptr.p, ND.d_idx, part, rb,
+                                              jb, P->lists[L_INTER].d_idx, P->d_xfer_dst,
+                                              msg_of.p, j0key.p);
+        CK(cudaGetLastError());
+    }
+
+    // ---- J0 (Eqs. L0, IL0) and the aggregator buffers b_{l->nl}
+    int64_t nj0 = cb.select(j0key.p, ngs, j0alt.p, NotSent{});
+    cb.sort(j0alt.p, j0key.p, nj0, 2 * rb + jb);
+    dvec<uint64_t> j0u(nj0);
+    int64_t Uj0 = cb.unique(j0alt.p, nj0, j0u.p);
+    make_list(cb, j0u.p, Uj0, rb, jb, P->lists[L_J0]);
+    if (Uj0) {
+        k_rekey_tj<<<blocks_for(Uj0), 256>>>(j0u.p, Uj0, rb, jb, j0key.p);
+        CK(cudaGetLastError());
+    }
+    cb.sort(j0key.p, j0alt.p, Uj0, rb + jb);
+    make_list(cb, j0key.p, Uj0, -1, jb, P->lists[L_LBUF]);
+    P->n_lbuf = Uj0;
+    j0key.alloc(0);
+    j0alt.alloc(0);
+    j0u.alloc(0);
+
+    std::vector<int32_t> lbuf_ptr = full_ptr(P->lists[L_LBUF], np);
+    std::vector<int32_t> bll_ptr = full_ptr(P->lists[L_BLL], np);
+    std::vector<int32_t> bnl_ptr = full_ptr(P->lists[L_BNL], np);
+    dvec<int32_t> d_lbuf_ptr, d_bll_ptr, d_bnl_ptr;
+    d_lbuf_ptr.p = upload(lbuf_ptr);
+    d_bll_ptr.p = upload(bll_ptr);
+    d_bnl_ptr.p = upload(bnl_ptr);
+    if (ngs) {
+        CK(cudaMalloc(&P->d_pack_src, sizeof(uint32_t) * ngs));
+        k_pack_src<<<blocks_for(ngs), 256>>>(ngs, P->lists[L_INTER].d_idx, msg_of.p, d_msg_src.p,
+                                            d_lbuf_ptr.p, P->lists[L_LBUF].d_idx, part,
+                                            P->d_pack_src, bad.p);
+        CK(cudaGetLastError());
+        check_bad(bad, "internal: pack source missing from the aggregator buffer");
+    }
+    msg_of.alloc(0);
+
+    // ---- J1 (Eqs. L1_send, IL1) and the unpack sources
+    const int64_t nbnl = P->n_bnl;
+    std::vector<uint64_t> pair_key(M);
+    for (int64_t k = 0; k < M; k++) pair_key[k] = ((uint64_t)ND.src[k] << nb) | ND.dst[k];
+    dvec<uint64_t> d_pair_key;
+    d_pair_key.p = upload(pair_key);
+    dvec<int32_t> d_recv_proc;
+    d_recv_proc.p = upload(P->recv_proc);
+    dvec<uint64_t> j1key(nbnl), j1alt(nbnl);
+    if (nbnl) {
+        CK(cudaMalloc(&P->d_unp_src, sizeof(int32_t) * nbnl));
+        k_unpack_src<<<blocks_for(nbnl), 256>>>(nbnl, bnl_keys.p, jb, part, ppn, nb, M,
+                                               d_pair_key.p, d_recv_proc.p, d_pair_gr_off.p,
+                                               d_node_ptr.p, ND.d_idx, rb, j1key.p,
+                                               P->d_unp_src, bad.p);
+        CK(cudaGetLastError());
+        check_bad(bad, "internal: off-node column without a node-pair message");
+    }
+    int64_t nj1 = cb.select(j1key.p, nbnl, j1alt.p, NotSent{});
+    cb.sort(j1alt.p, j1key.p, nj1, 2 * rb + jb);
+    make_list(cb, j1alt.p, nj1, rb, jb, P->lists[L_J1]);
+    j1key.alloc(0);
+    j1alt.alloc(0);
+    bnl_keys.alloc(0);
+
+    // ---- three-block CSR
+    CK(cudaMalloc(&P->d_rowptr, sizeof(int32_t) * (n + 1)));
+    CK(cudaMalloc(&P->d_colenc, sizeof(uint32_t) * std::max<int64_t>(nnz, 1) + 64));
+    CK(cudaMalloc(&P->d_val, sizeof(double) * std::max<int64_t>(nnz, 1) + 64));
+    CK(cudaMalloc(&P->d_split, sizeof(int32_t) * 3 * n));
+    if (P->flags & NAPSPMV_F32_VALUES)
+        CK(cudaMalloc(&P->d_val32, sizeof(float) * std::max<int64_t>(nnz, 1) + 64));
+    k_three_block<<<blocks_for(n), 256>>>(rp.p, n, col.p, val.p, tag.p, part, d_bll_ptr.p,
+                                         P->lists[L_BLL].d_idx, d_bnl_ptr.p,
+                                         P->lists[L_BNL].d_idx, P->d_colenc, P->d_val,
+                                         P->d_val32, P->d_split, P->d_rowptr, bad.p);
+    CK(cudaGetLastError());
+    check_bad(bad, "internal: column missing from its receive buffer");
+    CK(cudaDeviceSynchronize());
+
+    // ---- per-node ranges for cutting work items
+    P->node_bll.assign(nn + 1, 0);
+    P->node_lbuf.assign(nn + 1, 0);
+    P->node_bnl.assign(nn + 1, 0);
+    P->node_rows.assign(nn + 1, 0);
+    P->node_gs.assign(nn + 1, 0);
+    for (int32_t x = 0; x <= nn; x++) {
+        int32_t r = std::min<int64_t>((int64_t)x * ppn, np);
+        P->node_bll[x] = bll_ptr[r];
+        P->node_lbuf[x] = lbuf_ptr[r];
+        P->node_bnl[x] = bnl_ptr[r];
+        P->node_rows[x] = part.start(r);
+    }
+    {
+        int64_t i = 0;
+        for (int32_t x = 0; x <= nn; x++) {
+            int64_t first_rank = (int64_t)x * ppn;
+            while (i < M && msg_src[i] < first_rank) i++;
+            P->node_gs[x] = gs_off[i];
+        }
+    }
+    P->gs_msg_off = gs_off;
+    P->gs_msg_dstnode = msg_dstnode;
+    std::vector<int32_t> gs_off32(M + 1);
+    for (int64_t i = 0; i <= M; i++) gs_off32[i] = (int32_t)gs_off[i];
+    P->d_gs_msg_off = upload(gs_off32);
+    P->d_gs_msg_dstnode = upload(msg_dstnode);
+
+    host_stats(P);
+}
+
+}  // namespace
+
+void plan_free(napspmv_plan_t *P)
+{
+    if (!P) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(P->device);
+    if (P->ws) {
+        ws_free(P->ws);
+        delete P->ws;
+    }
+    for (auto &L : P->lists)
+        if (L.d_idx) cudaFree(L.d_idx);
+    void *ptrs[] = {P->d_split, P->d_rowptr, P->d_colenc, P->d_val, P->d_val32, P->d_pack_src,
+                    P->d_xfer_dst, P->d_unp_src, P->d_gs_msg_off, P->d_gs_msg_dstnode,
+                    P->items.d_items, P->items.d_cnt};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete P;
+    cudaSetDevice(cur);
+}
+
+int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
+                napspmv_plan_t **out)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!out) {
+        set_error(NAPSPMV_ERR_ARG, "out is NULL");
+        return NAPSPMV_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!A || A->n < 1 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && (!A->col || !A->val))) {
+        set_error(NAPSPMV_ERR_ARG, "invalid CSR descriptor");
+        return NAPSPMV_ERR_ARG;
+    }
+    if (np < 1 || np > A->n || ppn < 1) {
+        set_error(NAPSPMV_ERR_ARG, "need 1 <= n_p <= N and ppn >= 1");
+        return NAPSPMV_ERR_ARG;
+    }
+    if (A->n >= (1ll << 30) || A->nnz >= (1ll << 31) - 64) {
+        set_error(NAPSPMV_ERR_UNSUPPORTED, "N must be < 2^30 and nnz < 2^31");
+        return NAPSPMV_ERR_UNSUPPORTED;
+    }
+    napspmv_plan_t *P = new napspmv_plan_t();
+    P->n = A->n;
+    P->nnz = A->nnz;
+    P->np = np;
+    P->ppn = ppn;
+    P->nn = (np + ppn - 1) / ppn;
+    P->flags = flags;
+    try {
+        CK(cudaGetDevice(&P->device));
+        CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
+        build(P, A);
+        P->ws = new napspmv_ws_t();
+        int rc = ws_alloc(P, P->ws);
+        if (rc) throw NapError{rc, "workspace allocation failed"};
+        P->ws->owned_by_plan = true;
+        // defaults: lanes per row from the mean row length
+        double avg = (double)P->nnz / (double)P->n;
+        int vec = avg <= 2.5 ? 1 : avg <= 5 ? 2 : avg <= 12 ? 4 : avg <= 24 ? 8 : avg <= 48 ? 16 : 32;
+        P->defaults.precision = NAPSPMV_PREC_F64;
+        P->defaults.engine = NAPSPMV_ENGINE_FUSED;
+        P->defaults.vec = vec;
+        P->defaults.ctas_per_sm = 0;  // occupancy maximum
+        P->defaults.chunk = 4096;
+        P->defaults.tile_rows = 1024;
+        P->defaults.timeout_ms = 10000;
+        P->defaults.debug_stall = 0;
+        rc = build_items(P, P->defaults.chunk, P->defaults.tile_rows);
+        if (rc) throw NapError{rc, "work-item construction failed"};
+    } catch (const NapError &e) {
+        plan_free(P);
+        set_error(e.code, e.msg);
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        plan_free(P);
+        set_error(NAPSPMV_ERR_OOM, "host allocation failed");
+        return NAPSPMV_ERR_OOM;
+    }
+    P->stats.plan_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = P;
+    return NAPSPMV_OK;
+}
+
+}  // namespace nap

@@ -1,0 +1,167 @@
+"""The node-aware apply on the GPU (through the C ABI) against the CPU oracle.
+
+FP64: elementwise |w - w_ref| <= 1e-13 (|A||v|)_i and normwise relative error
+<= 1e-13.  FP32-stored values: within 1e-13 of the oracle's FP32-product /
+FP64-sum result and <= 1e-6 normwise of the FP64 product."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_util import abs_row_bound, assert_close_fp64, gpu_plan, oracle_chain
+from paper_1612_08060_gb300 import inputs as I
+from paper_1612_08060_gb300 import napspmv as nap
+
+pytestmark = pytest.mark.gpu
+
+
+def run(plan, v, reps=1, scale=1.0, **opts):
+    vd = torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    wd = torch.full_like(vd, float("nan"))
+    o = nap.make_opts(**opts) if opts else None
+    nap.napspmv_apply_ex(plan, vd, wd, reps, scale, o)
+    assert nap.napspmv_status(plan) == 0
+    return wd.cpu().numpy()
+
+
+ENGINES = [dict(engine=nap.ENGINE_FUSED), dict(engine=nap.ENGINE_PHASED)]
+SHAPES = [dict(vec=v) for v in (1, 2, 4, 8, 32)]
+
+
+@pytest.mark.parametrize("eng", ENGINES)
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("n,dens,n_p,ppn", [(64, 0.1, 8, 3), (300, 0.02, 37, 4),
+                                             (1000, 0.01, 1000, 16), (513, 0.03, 1, 1)])
+def test_random_fp64(eng, shape, n, dens, n_p, ppn):
+    A = I.random_pattern(n, dens, n + n_p)
+    v = I.vector(n, 5)
+    w = run(gpu_plan(A, n_p, ppn), v, **eng, **shape)
+    assert_close_fp64(w, O.spmv(A.row_ptr, A.col, A.val, v), abs_row_bound(A, v))
+
+
+@pytest.mark.parametrize("eng", ENGINES)
+@pytest.mark.parametrize("chunk,tile", [(32, 1), (64, 7), (4096, 1024), (100000, 100000)])
+def test_item_sizes(eng, chunk, tile):
+    w_ = I.workload(1)
+    A = w_.build()
+    v = I.vector(A.n, w_.seed)
+    w = run(gpu_plan(A, w_.n_p, w_.ppn), v, chunk=chunk, tile_rows=tile, **eng)
+    assert_close_fp64(w, O.spmv(A.row_ptr, A.col, A.val, v), abs_row_bound(A, v))
+
+
+@pytest.mark.parametrize("eng", ENGINES)
+@pytest.mark.parametrize("reps", [2, 3, 10])
+def test_chained(eng, reps):
+    A = I.poisson3d(20)
+    v = I.vector(A.n, 9)
+    plan = gpu_plan(A, 40, 4)
+    w = run(plan, v, reps=reps, scale=1.0 / 12.0, **eng)
+    ref = oracle_chain(A, v, reps, 1.0 / 12.0)
+    assert np.linalg.norm(w - ref) <= 1e-13 * reps * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("eng", ENGINES)
+def test_fp32_values(eng):
+    A = I.aniso_q1(96)
+    v = I.vector(A.n, 13)
+    plan = gpu_plan(A, 18, 4)
+    w = run(plan, v, precision=nap.PREC_F32, **eng)
+    ref32 = O.spmv_f32(A.row_ptr, A.col, A.val.astype(np.float32), v)
+    ref64 = O.spmv(A.row_ptr, A.col, A.val, v)
+    assert np.linalg.norm(w - ref32) <= 1e-13 * np.linalg.norm(ref32)
+    assert np.linalg.norm(w - ref64) <= 1e-6 * np.linalg.norm(ref64)
+
+
+def test_fp32_requires_flag():
+    A = I.poisson2d(8)
+    plan = nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, 0)
+    vd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(nap.NapError) as e:
+        nap.napspmv_apply_ex(plan, vd, torch.empty_like(vd), 1, 1.0,
+                             nap.make_opts(precision=nap.PREC_F32))
+    assert e.value.code == nap.ERR_STATE
+
+
+@pytest.mark.parametrize("eng", ENGINES)
+def test_edge_cases(eng):
+    # nnz = 0
+    n = 37
+    A = I.CSR(np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    w = run(gpu_plan(A, 5, 2), I.vector(n, 1), **eng)
+    assert np.array_equal(w, np.zeros(n))
+    # empty rows, uneven partition, partial last node, ppn > n_p
+    B = I.random_pattern(101, 0.05, 17, diag=False)
+    v = I.vector(101, 2)
+    for n_p, ppn in [(7, 3), (10, 64), (101, 1), (1, 5)]:
+        w = run(gpu_plan(B, n_p, ppn), v, **eng)
+        assert_close_fp64(w, O.spmv(B.row_ptr, B.col, B.val, v), abs_row_bound(B, v))
+    # one dense row among short ones (long-row lane reduction)
+    C = I.random_pattern(200, 0.01, 4)
+    rows = [set(C.col[C.row_ptr[i]:C.row_ptr[i + 1]]) for i in range(200)]
+    rows[77] = set(range(200))
+    rp = np.zeros(201, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([j for r in rows for j in sorted(r)], np.int32)
+    D = I.CSR(rp, col, np.random.default_rng(5).uniform(-1, 1, len(col)))
+    v = I.vector(200, 3)
+    for vec in (1, 4, 32):
+        w = run(gpu_plan(D, 9, 2), v, vec=vec, **eng)
+        assert_close_fp64(w, O.spmv(D.row_ptr, D.col, D.val, v), abs_row_bound(D, v))
+
+
+def test_engines_agree_bitwise():
+    """Both engines evaluate every row in the same order: identical bits."""
+    A = I.aniso_q1(64)
+    v = I.vector(A.n, 21)
+    plan = gpu_plan(A, 16, 4)
+    a = run(plan, v, engine=nap.ENGINE_FUSED, vec=4)
+    b = run(plan, v, engine=nap.ENGINE_PHASED, vec=4)
+    assert np.array_equal(a, b)
+
+
+def test_host_entry_point():
+    A = I.poisson2d(40)
+    v = I.vector(A.n, 4)
+    plan = gpu_plan(A, 10, 2)
+    w = np.zeros(A.n)
+    nap.napspmv_apply_host(plan, v, w, 3, 0.125)
+    ref = oracle_chain(A, v, 3, 0.125)
+    assert np.linalg.norm(w - ref) <= 3e-13 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+def test_workloads_full_size(cfg):
+    """Full-size stencil workloads, default (bench) launch options, one apply;
+    every output element compared."""
+    w_ = I.workload(cfg)
+    A = w_.build()
+    v = I.vector(A.n, w_.seed)
+    plan = gpu_plan(A, w_.n_p, w_.ppn)
+    w = run(plan, v)
+    assert_close_fp64(w, O.spmv(A.row_ptr, A.col, A.val, v), abs_row_bound(A, v))
+
+
+def test_config2_chain_bench_configuration():
+    """The benchmark's step: 100 chained applies x <- A x / 12 of the 3D 7-point
+    128^3 workload in one persistent launch; every element compared with the
+    oracle's chain."""
+    w_ = I.workload(2)
+    A = w_.build()
+    v = I.vector(A.n, w_.seed)
+    plan = gpu_plan(A, w_.n_p, w_.ppn)
+    w = run(plan, v, reps=100, scale=1.0 / 12.0)
+    ref = oracle_chain(A, v, 100, 1.0 / 12.0)
+    assert np.linalg.norm(w - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_config3_fp32_error_stated():
+    """Config 3 (rotated anisotropic Q1, 2048^2): FP32-stored values stay within
+    1e-6 (normwise) of the FP64 oracle."""
+    w_ = I.workload(3)
+    A = w_.build()
+    v = I.vector(A.n, w_.seed)
+    plan = gpu_plan(A, w_.n_p, w_.ppn)
+    w = run(plan, v, precision=nap.PREC_F32)
+    ref = O.spmv(A.row_ptr, A.col, A.val, v)
+    rel = np.linalg.norm(w - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-6, rel

@@ -1,0 +1,41 @@
+"""Failure detection without a GPU fault: a dependency wait that nothing
+satisfies (the debug_stall hook makes the first work item wait on a counter no
+item increments) ends after timeout_ms with NAPSPMV_ERR_TIMEOUT, the context
+stays usable and the next apply is correct."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_util import abs_row_bound, assert_close_fp64, gpu_plan
+from paper_1612_08060_gb300 import inputs as I
+from paper_1612_08060_gb300 import napspmv as nap
+
+pytestmark = pytest.mark.gpu
+
+
+def test_stalled_wait_times_out_and_recovers():
+    A = I.poisson2d(32)
+    plan = gpu_plan(A, 8, 2)
+    v = I.vector(A.n, 1)
+    vd = torch.from_numpy(v).cuda()
+    wd = torch.empty_like(vd)
+    nap.napspmv_apply_ex(plan, vd, wd, 3, 1.0, nap.make_opts(debug_stall=1, timeout_ms=100))
+    assert nap.napspmv_status(plan) == nap.ERR_TIMEOUT
+    assert nap.napspmv_status(plan) == nap.OK  # the status was cleared
+    nap.napspmv_apply(plan, vd, wd)
+    assert nap.napspmv_status(plan) == nap.OK
+    assert_close_fp64(wd.cpu().numpy(), O.spmv(A.row_ptr, A.col, A.val, v), abs_row_bound(A, v))
+
+
+def test_sticky_error_skips_work_until_cleared():
+    A = I.poisson2d(16)
+    plan = gpu_plan(A, 4, 2)
+    vd = torch.ones(A.n, dtype=torch.float64, device="cuda")
+    wd = torch.full_like(vd, 7.0)
+    nap.napspmv_apply_ex(plan, vd, wd, 1, 1.0, nap.make_opts(debug_stall=1, timeout_ms=50))
+    torch.cuda.synchronize()
+    w2 = torch.full_like(vd, 7.0)
+    nap.napspmv_apply(plan, vd, w2)  # sees the sticky flag and does no work
+    assert nap.napspmv_status(plan) == nap.ERR_TIMEOUT
+    assert torch.all(w2 == 7.0)
