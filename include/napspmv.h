@@ -99,7 +99,10 @@ typedef struct {
     int32_t vec;         /* lanes per matrix row: 1, 2, 4, 8, 16 or 32         */
     int32_t ctas_per_sm; /* persistent CTAs per SM (fused engine)              */
     int32_t chunk;       /* gather elements per work item (fused engine)       */
-    int32_t tile_rows;   /* matrix rows per work item (fused engine)           */
+    int32_t tile_rows;   /* at most this many matrix rows per SpMV work item   */
+    int32_t tile_nnz;    /* at most this many stored entries per SpMV work item
+                            (their products are staged in shared memory); a
+                            longer single row gets a tile of its own           */
     int32_t timeout_ms;  /* limit of every device-side wait                    */
     int32_t debug_stall; /* test hook: 1 makes the first work item wait on a
                             counter nothing increments, so the launch ends
@@ -240,6 +243,39 @@ int napspmv_cg_ir(napspmv_plan_t *P, const double *b, double *x, double rtol, do
 /* Plain FP64 CG (no refinement), same conventions; for comparison. */
 int napspmv_cg(napspmv_plan_t *P, const double *b, double *x, double rtol, int32_t max_it,
                napspmv_cg_info *info, void *stream);
+
+/* One conjugate-gradient solve among several served together: its plan and
+ * workspace (NULL = the plan's own; slots of one call must not share one),
+ * the right-hand side b and device vectors x, r, p, q of N values, and 8
+ * device doubles of scalars: [0] r.r, [1] p.q, [2] alpha, [3] beta,
+ * [4] latest r.r, [5] b.b.  Not in the paper: the batched form of the
+ * request server; each slot's arithmetic does not depend on the others in
+ * the call (fixed per-slot reduction order). */
+typedef struct {
+    napspmv_plan_t *plan;
+    napspmv_ws_t *ws;
+    const double *b;
+    double *x, *r, *p, *q;
+    double *scal;
+} napspmv_cg_slot;
+
+/* For every slot: r = b - A x (apply at `precision`), p = r, scal[0] = r.r,
+ * scal[5] = b.b.  With x_is_zero the apply is skipped and x is set to 0.
+ * count <= 64.  Asynchronous. */
+int napspmv_cg_batch_init(int32_t count, const napspmv_cg_slot *slots, int32_t precision,
+                          int32_t x_is_zero, void *stream);
+
+/* `iters` CG iterations for every slot: q = A p (one batched apply for all
+ * slots), alpha = r.r / p.q, x += alpha p, r -= alpha q, beta = r.r_new /
+ * r.r, p = r + beta p.  Asynchronous; the caller reads scal[0] to decide
+ * convergence. */
+int napspmv_cg_batch_iterate(int32_t count, const napspmv_cg_slot *slots, int32_t precision,
+                             int32_t iters, void *stream);
+
+/* y_i += x_i for count <= 64 pairs of device vectors of n_i values (the
+ * refinement update x += d of served CG-IR solves).  Asynchronous. */
+int napspmv_batch_add(int32_t count, double *const *y, const double *const *x, const int64_t *n,
+                      void *stream);
 
 /* Deterministic FP64 dot product of two device vectors of length n (fixed
  * partition and summation order, so the result does not depend on timing).

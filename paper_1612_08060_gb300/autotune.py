@@ -1,0 +1,103 @@
+"""Launch-option autotuner for the node-aware apply.
+
+Searches lanes per row (``vec``), the SpMV tile shape (``tile_rows``,
+``tile_nnz`` = shared-memory staging of the products), the gather chunk of the
+message steps (``chunk``) and CTAs per SM by coordinate descent: starting from the
+plan's defaults, each parameter in turn is set to each candidate while the
+others stay fixed, the fastest is kept, and the sweep repeats until nothing
+improves.  Each candidate is timed with CUDA events over chained applies
+(inputs already on the device).  The winner is installed with
+napspmv_set_default_opts and cached per (N, nnz, nnz-per-row histogram, n_p,
+ppn, precision) key, in memory and optionally in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from . import napspmv as nap
+
+CANDIDATES = {
+    "vec": [1, 2, 4, 8, 16],
+    "tile_nnz": [2048, 4096, 8192],
+    "tile_rows": [256, 512, 1024, 2048],
+    "chunk": [1024, 2048, 4096, 8192, 16384],
+    "ctas_per_sm": [2, 3, 4, 5],
+}
+
+_cache: dict = {}
+
+
+def matrix_key(row_ptr, n_p, ppn, precision):
+    lens = np.diff(np.asarray(row_ptr))
+    hist = np.histogram(np.minimum(lens, 64), bins=[0, 2, 4, 8, 12, 16, 24, 32, 48, 65])[0]
+    hist = tuple(int(round(10 * h / max(1, len(lens)))) for h in hist)
+    return f"n{len(lens)}_nnz{int(lens.sum())}_h{hist}_np{n_p}_ppn{ppn}_p{precision}"
+
+
+def time_opts(plan, v, w, opts, reps=20, trials=3, stream=None):
+    import torch
+    s = stream or torch.cuda.current_stream()
+    nap.napspmv_apply_ex(plan, v, w, reps, 1.0 / 16.0, opts, stream=s)  # warm-up
+    best = float("inf")
+    for _ in range(trials):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        nap.napspmv_apply_ex(plan, v, w, reps, 1.0 / 16.0, opts, stream=s)
+        b.record(s)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b) / reps)
+    if nap.napspmv_status(plan, s) != 0:
+        return float("inf")
+    return best  # ms per apply
+
+
+def tune(plan, row_ptr, precision=nap.PREC_F64, reps=20, max_sweeps=2, cache_file=None,
+         verbose=False):
+    """Tune `plan` in place; returns (best options dict, ms per apply)."""
+    import torch
+    key = matrix_key(row_ptr, plan.n_p, plan.ppn, precision)
+    if cache_file and os.path.exists(cache_file) and not _cache:
+        _cache.update(json.load(open(cache_file)))
+    if key in _cache:
+        best = dict(_cache[key]["opts"])
+        nap.napspmv_set_default_opts(plan, nap.make_opts(precision=precision, **best))
+        return best, _cache[key]["ms"]
+    d = nap.napspmv_get_default_opts(plan)
+    cur = {k: int(getattr(d, k)) for k in CANDIDATES}
+    if cur["ctas_per_sm"] == 0:
+        cur["ctas_per_sm"] = 5
+    v = torch.rand(plan.n, dtype=torch.float64, device="cuda") * 2 - 1
+    w = torch.empty_like(v)
+
+    def measure(c):
+        try:
+            o = nap.make_opts(precision=precision, engine=nap.ENGINE_FUSED, **c)
+            return time_opts(plan, v, w, o, reps=reps)
+        except nap.NapError:
+            return float("inf")
+
+    best_ms = measure(cur)
+    for _ in range(max_sweeps):
+        improved = False
+        for k, cands in CANDIDATES.items():
+            for val in cands:
+                if val == cur[k]:
+                    continue
+                trial = dict(cur, **{k: val})
+                ms = measure(trial)
+                if verbose:
+                    print(f"  {trial} -> {ms:.4f} ms")
+                if ms < best_ms * 0.99:
+                    best_ms, cur, improved = ms, trial, True
+        if not improved:
+            break
+    nap.napspmv_set_default_opts(plan, nap.make_opts(precision=precision, **cur))
+    _cache[key] = {"opts": cur, "ms": best_ms}
+    if cache_file:
+        with open(cache_file, "w") as f:
+            json.dump(_cache, f, indent=1)
+    return cur, best_ms

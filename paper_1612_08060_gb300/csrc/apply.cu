@@ -9,8 +9,8 @@
 //   phase 3  inter-node transfer g_send -> g_recv (the "network")
 //   phase 4  off_node -> on_node  b_{nl->l}[k] = g_recv[unp_src[k]] (Eq. IL1)
 //   phase 5  three-block SpMV: on_process from x, on_node from b_{l->l},
-//            off_node from b_{nl->l} (three local_spmv of the algorithm in one
-//            pass over each row)
+//            off_node from b_{nl->l} (the three local_spmv of the algorithm as
+//            one pass over each row, blocks in that order)
 //
 // Fused engine: one persistent launch.  CTAs take work items (chunks of a
 // node's gather ranges, tiles of a node's rows) from a global ticket counter
@@ -21,10 +21,16 @@
 // handed out in order and an item only waits on earlier tickets, so progress
 // never depends on how many CTAs are resident.
 //
-// Phased engine (control): one kernel per phase per apply.
+// A row tile is evaluated in two passes: every thread forms products
+// a_k * x_{c_k} of the tile's entries with independent loads (coalesced
+// column/value streams, gathered x) into shared memory, then the rows are
+// summed from shared memory in stored order.
+//
+// Phased engine (control): one kernel per phase per apply, same tiles and the
+// same arithmetic, so the two engines agree bit for bit.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "internal.h"
 
@@ -47,29 +53,32 @@ int cuda_error(cudaError_t e, const char *what)
 }
 void count_launch(int64_t n) { g_launches += n; }
 
+constexpr int NT = 256;  // threads per CTA of every apply kernel
+
 // ---------------------------------------------------------- PTX helpers
+// Read-only streams (matrix, index arrays): non-coherent path, no L1 allocation.
 __device__ __forceinline__ uint32_t ld_stream_u32(const uint32_t *p)
 {
     uint32_t v;
-    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ int32_t ld_stream_s32(const int32_t *p)
 {
     int32_t v;
-    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ double ld_stream_f64(const double *p)
 {
     double v;
-    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ float ld_stream_f32(const float *p)
 {
     float v;
-    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
@@ -95,6 +104,32 @@ __device__ __forceinline__ double ldx(const double *p)
     return __ldg(p);
 }
 
+// Batched element loop over [b, e): U independent index loads, then U
+// independent data loads, then U stores, per thread and step.
+template <int U, class LoadIdx, class LoadVal, class Store>
+__device__ __forceinline__ void batched(int b, int e, int tid, LoadIdx li, LoadVal lv, Store st)
+{
+    for (int base = b + tid; base < e; base += NT * U) {
+        uint32_t ix[U];
+        double vv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = base + u * NT;
+            if (k < e) ix[u] = li(k);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = base + u * NT;
+            if (k < e) vv[u] = lv(k, ix[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = base + u * NT;
+            if (k < e) st(k, ix[u], vv[u]);
+        }
+    }
+}
+
 // ------------------------------------------------------- three-block SpMV
 struct Csr3 {
     const int32_t *rowptr;
@@ -103,42 +138,265 @@ struct Csr3 {
     const float *val32;
 };
 
-// Rows [r0, r1): V lanes per row, 256 threads.  All lanes of a warp run the
-// same number of outer iterations, so the shuffle reduction is convergent.
-template <int V, bool F32, bool INKERNEL>
-__device__ __forceinline__ void spmv_rows(const Csr3 &A, const double *x, const double *bll,
-                                          const double *bnl, double *y, double scale, int r0,
-                                          int r1, int tid, int nthreads)
+template <bool INKERNEL>
+__device__ __forceinline__ double load_x(uint32_t c, const double *x, const double *bll,
+                                         const double *bnl)
 {
-    const int lane = tid & (V - 1);
-    const int grp = tid / V;
-    const int groups = nthreads / V;
-    for (int base = r0; base < r1; base += groups) {
-        const int row = base + grp;
+    const uint32_t blk = c >> kBlockShift;
+    const double *src = blk == 0 ? x : (blk == 1 ? bll : bnl);
+    return ldx<INKERNEL>(src + (c & kIndexMask));
+}
+
+// Scaling of a row result: exact exponent arithmetic when scale is a power
+// of two and the result stays normal (no FP64 instruction), else one DMUL.
+struct Scale {
+    double s;
+    int e2;  // scale = 2^e2, or kNoPow2
+};
+constexpr int kNoPow2 = 1 << 30;
+__device__ __forceinline__ double apply_scale(double acc, const Scale sc)
+{
+    if (sc.s == 1.0) return acc;
+    if (sc.e2 != kNoPow2) {
+        const long long bits = __double_as_longlong(acc);
+        const int ex = (int)((bits >> 52) & 0x7ff);
+        if (ex > 0 && ex < 0x7ff && ex + sc.e2 > 0 && ex + sc.e2 < 0x7ff)
+            return __longlong_as_double(bits + ((long long)sc.e2 << 52));
+    }
+    return __dmul_rn(sc.s, acc);
+}
+
+__device__ __forceinline__ uint4 ld_stream_v4u32(const uint32_t *p)
+{
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_stream_v2f64(const double *p)
+{
+    double2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream_v4f32(const float *p)
+{
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+
+// ------------------------------------------- TMA-staged three-block SpMV
+// A row tile's slices of the row pointer, column and value arrays are brought
+// into shared memory by bulk asynchronous copies (cp.async.bulk, completion
+// counted on an mbarrier), two stages per CTA, so the copy of the next tile
+// overlaps the current one.  Slices are widened to 16-byte boundaries (the
+// arrays are padded for that).  Each row is then summed by V lanes straight
+// from shared memory, gathering x from HBM / L2: one DFMA per stored entry.
+
+struct StageLayout {  // byte offsets inside one stage
+    int rows, col, val, bytes;
+};
+__host__ __device__ __forceinline__ int align16(int b) { return (b + 15) & ~15; }
+__host__ __device__ __forceinline__ StageLayout stage_layout(int cap, int tile_rows)
+{
+    StageLayout L;
+    L.rows = 0;
+    L.col = align16(4 * (tile_rows + 8));
+    L.val = L.col + align16(4 * (cap + 8));
+    L.bytes = L.val + align16(8 * (cap + 8));
+    return L;
+}
+constexpr int kStages = 2;
+constexpr int kMbarBytes = 16 * kStages;  // one 8-byte mbarrier per stage, 16-byte slots
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, "
+        "1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+struct TileStage {
+    uint64_t *bar;
+    int *rows;
+    uint32_t *col;
+    double *val;  // FP32 mode stores floats here
+};
+
+__device__ __forceinline__ TileStage tile_stage(unsigned char *base, int s, int cap, int tile_rows)
+{
+    const StageLayout L = stage_layout(cap, tile_rows);
+    unsigned char *p = base + kMbarBytes + s * L.bytes;
+    TileStage t;
+    t.bar = reinterpret_cast<uint64_t *>(base + 16 * s);
+    t.rows = reinterpret_cast<int *>(p + L.rows);
+    t.col = reinterpret_cast<uint32_t *>(p + L.col);
+    t.val = reinterpret_cast<double *>(p + L.val);
+    return t;
+}
+
+// One thread: start the copies of the tile's slices into stage `st`.
+template <bool F32>
+__device__ __forceinline__ void tile_issue(const Csr3 &A, const TileStage &st, int r0, int r1,
+                                           int k0, int k1)
+{
+    const int rb = r0 & ~3, re = (r1 + 1 + 3) & ~3;
+    const int kb = k0 & ~3, ke = (k1 + 3) & ~3;
+    const uint32_t brow = 4u * (re - rb), bcol = 4u * (ke - kb), bval = (F32 ? 4u : 8u) * (ke - kb);
+    fence_proxy_async();  // earlier generic reads of this stage are ordered before the copies
+    mbar_expect_tx(st.bar, brow + bcol + bval);
+    bulk_g2s(st.rows, A.rowptr + rb, brow, st.bar);
+    if (bcol) {
+        bulk_g2s(st.col, A.colenc + kb, bcol, st.bar);
+        if (F32)
+            bulk_g2s(st.val, A.val32 + kb, bval, st.bar);
+        else
+            bulk_g2s(st.val, A.val + kb, bval, st.bar);
+    }
+}
+
+// All threads: wait for the stage's copies (bounded).  On a timeout the error
+// flag is set, the wait continues (bounded again) so that no copy is left in
+// flight, and false is returned.
+__device__ __forceinline__ bool tile_wait(const TileStage &st, uint32_t parity, int *err)
+{
+    constexpr long long kLimitNs = 2000000000ll;  // 2 s; a healthy copy takes microseconds
+    if (mbar_try_wait(st.bar, parity)) return true;
+    long long t0 = globaltimer();
+    for (;;) {
+        for (int i = 0; i < 256; i++)
+            if (mbar_try_wait(st.bar, parity)) return true;
+        if (globaltimer() - t0 > kLimitNs) break;
+    }
+    atomicCAS(err, 0, 2);
+    t0 = globaltimer();
+    for (;;) {
+        for (int i = 0; i < 256; i++)
+            if (mbar_try_wait(st.bar, parity)) return false;
+        if (globaltimer() - t0 > kLimitNs) return false;
+    }
+}
+
+// Rows [r0, r1) from a staged tile.
+template <int V, bool F32, bool INKERNEL>
+__device__ __forceinline__ void tile_compute(const TileStage &st, const double *x, const double *bll,
+                                             const double *bnl, double *y, const Scale sc, int r0,
+                                             int r1, int k0, int tid)
+{
+    const int rb = r0 & ~3, kb = k0 & ~3;
+    const int nr = r1 - r0;
+    const int lane = tid & (V - 1), grp = tid / V, groups = NT / V;
+    const float *val32 = reinterpret_cast<const float *>(st.val);
+    for (int base = 0; base < nr; base += groups) {
+        const int i = base + grp;
         double acc = 0.0;
-        if (row < r1) {
-            const int s = ld_stream_s32(A.rowptr + row), e = ld_stream_s32(A.rowptr + row + 1);
-#pragma unroll 2
+        if (i < nr) {
+            const int s = st.rows[r0 - rb + i] - kb, e = st.rows[r0 - rb + i + 1] - kb;
+#pragma unroll 4
             for (int k = s + lane; k < e; k += V) {
-                const uint32_t c = ld_stream_u32(A.colenc + k);
-                const uint32_t blk = c >> kBlockShift;
-                const double *src = blk == 0 ? x : (blk == 1 ? bll : bnl);
-                const double xv = ldx<INKERNEL>(src + (c & kIndexMask));
-                if (F32) {
-                    const float a = ld_stream_f32(A.val32 + k);
-                    const float p = __fmul_rn(a, __double2float_rn(xv));
-                    acc = __dadd_rn(acc, (double)p);
-                } else {
-                    acc = fma(ld_stream_f64(A.val + k), xv, acc);
-                }
+                const double xv = load_x<INKERNEL>(st.col[k], x, bll, bnl);
+                if (F32)
+                    acc = __dadd_rn(acc, (double)__fmul_rn(val32[k], __double2float_rn(xv)));
+                else
+                    acc = fma(st.val[k], xv, acc);
             }
         }
         if (V > 1) {
 #pragma unroll
-            for (int o = V / 2; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+            for (int o = V / 2; o > 0; o >>= 1)
+                acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
         }
-        if (row < r1 && lane == 0) y[row] = scale == 1.0 ? acc : scale * acc;
+        if (i < nr && lane == 0) y[r0 + i] = apply_scale(acc, sc);
     }
+}
+
+// A single row with more stored entries than a stage holds: read straight from
+// global memory, the whole CTA on the row (fixed strides, fixed-order tree).
+template <bool F32, bool INKERNEL>
+__device__ void row_direct(const Csr3 &A, const double *x, const double *bll, const double *bnl,
+                           double *y, const Scale sc, int r0, int r1, double *red, int tid)
+{
+    for (int i = r0; i < r1; i++) {
+        const int s = ld_stream_s32(A.rowptr + i), e = ld_stream_s32(A.rowptr + i + 1);
+        double acc = 0.0;
+        for (int k = s + tid; k < e; k += NT) {
+            const double xv = load_x<INKERNEL>(ld_stream_u32(A.colenc + k), x, bll, bnl);
+            if (F32)
+                acc = __dadd_rn(acc, (double)__fmul_rn(ld_stream_f32(A.val32 + k),
+                                                       __double2float_rn(xv)));
+            else
+                acc = fma(ld_stream_f64(A.val + k), xv, acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        if ((tid & 31) == 0) red[tid >> 5] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < NT / 32; q++) t = __dadd_rn(t, red[q]);
+            y[i] = apply_scale(t, sc);
+        }
+        __syncthreads();
+    }
+}
+
+// Shared memory of the apply kernels: the two mbarriers, two stages, and a
+// small reduction area for row_direct.
+__host__ __device__ __forceinline__ int tile_smem_bytes(int cap, int tile_rows)
+{
+    return kMbarBytes + kStages * stage_layout(cap, tile_rows).bytes + 8 * (NT / 32);
+}
+__device__ __forceinline__ double *tile_red(unsigned char *base, int cap, int tile_rows)
+{
+    return reinterpret_cast<double *>(base + kMbarBytes + kStages * stage_layout(cap, tile_rows).bytes);
+}
+__device__ __forceinline__ void tile_smem_init(unsigned char *base)
+{
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) mbar_init(reinterpret_cast<uint64_t *>(base + 16 * s), 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------- fused engine
@@ -146,7 +404,7 @@ struct Job {
     const Item *items;
     int32_t n_items;
     int32_t reps;
-    double scale;
+    Scale scale;
     long long tbase;  // first ticket of this job in the launch
     Csr3 A;
     const int32_t *bll_j, *lbuf_j, *xfer_dst, *unp_src;
@@ -165,6 +423,8 @@ template <int MAXJ>
 struct FusedParams {
     int32_t njobs;
     int32_t stall;
+    int32_t cap;        // tile capacity in stored entries (shared-memory stage)
+    int32_t tile_rows;  // tile capacity in rows
     long long total;
     long long timeout_ns;
     unsigned long long *ticket;
@@ -176,11 +436,11 @@ __device__ __forceinline__ bool wait_ge(const unsigned long long *p, unsigned lo
 {
     if (target == 0 || ld_acquire(p) >= target) return true;
     const long long t0 = globaltimer();
-    unsigned ns = 64;
+    unsigned ns = 32;
     for (;;) {
         if (*(volatile int *)err) return false;
         __nanosleep(ns);
-        if (ns < 2048) ns <<= 1;
+        if (ns < 1024) ns <<= 1;
         if (ld_acquire(p) >= target) return true;
         if (globaltimer() - t0 > timeout_ns) {
             atomicCAS(err, 0, 1);
@@ -189,7 +449,7 @@ __device__ __forceinline__ bool wait_ge(const unsigned long long *p, unsigned lo
     }
 }
 
-__device__ bool item_deps(const Job &J, const Item &it, int k, long long tmo, bool stall)
+__device__ __noinline__ bool item_deps(const Job &J, const Item &it, int k, long long tmo, bool stall)
 {
     auto C = [&](int c, int node) { return J.ctr + 1 + c * J.nn + node; };
     auto N = [&](int c, int node) { return (unsigned long long)J.cnt[c * J.nn + node]; };
@@ -226,7 +486,7 @@ __device__ bool item_deps(const Job &J, const Item &it, int k, long long tmo, bo
     }
 }
 
-__device__ void item_signal(const Job &J, const Item &it)
+__device__ __noinline__ void item_signal(const Job &J, const Item &it)
 {
     auto C = [&](int c, int node) { return J.ctr + 1 + c * J.nn + node; };
     switch (it.kind) {
@@ -245,102 +505,210 @@ __device__ void item_signal(const Job &J, const Item &it)
     }
 }
 
-template <int V, bool F32, int MAXJ>
-__global__ void __launch_bounds__(256) k_fused(const __grid_constant__ FusedParams<MAXJ> prm)
+// The element work of the message steps (shared by both engines).
+template <bool INKERNEL>
+__device__ __noinline__ void step_gather(double *dst, const double *src, const int32_t *idx,
+                                            int b, int e, int tid)
 {
-    __shared__ long long s_t;
+    batched<4>(
+        b, e, tid, [&](int k) { return (uint32_t)ld_stream_s32(idx + k); },
+        [&](int, uint32_t j) { return ldx<INKERNEL>(src + j); },
+        [&](int k, uint32_t, double v) { dst[k] = v; });
+}
+template <bool INKERNEL>
+__device__ __noinline__ void step_pack(double *gsend, const double *x, const double *lbuf,
+                                          const uint32_t *src, int b, int e, int tid)
+{
+    batched<4>(
+        b, e, tid, [&](int k) { return ld_stream_u32(src + k); },
+        [&](int, uint32_t u) {
+            return (u & kFromLbuf) ? ldx<INKERNEL>(lbuf + (u & ~kFromLbuf)) : ldx<INKERNEL>(x + u);
+        },
+        [&](int k, uint32_t, double v) { gsend[k] = v; });
+}
+template <bool INKERNEL>
+__device__ __noinline__ void step_transfer(double *grecv, const double *gsend,
+                                              const int32_t *dst, int b, int e, int tid)
+{
+    batched<4>(
+        b, e, tid, [&](int k) { return (uint32_t)ld_stream_s32(dst + k); },
+        [&](int k, uint32_t) { return ldx<INKERNEL>(gsend + k); },
+        [&](int, uint32_t d, double v) { grecv[d] = v; });
+}
+
+__device__ __forceinline__ bool staged_tile(const Item &it, int cap)
+{
+    return it.kind == kSpmv && it.k1 - it.k0 <= cap;
+}
+
+template <int MAXJ>
+__device__ __forceinline__ const Job &job_of(const FusedParams<MAXJ> &prm, long long t)
+{
+    int ji = 0;
+    if (MAXJ > 1)
+        while (ji + 1 < prm.njobs && prm.jobs[ji + 1].tbase <= t) ji++;
+    return prm.jobs[MAXJ > 1 ? ji : 0];
+}
+
+template <int V, bool F32, int MAXJ>
+__global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedParams<MAXJ> prm)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_t, s_next;
     __shared__ int s_ok;
     const int tid = threadIdx.x;
+    const int cap = prm.cap, trows = prm.tile_rows;
+    tile_smem_init(smem);
+    double *red = tile_red(smem, cap, trows);
+    uint32_t phase = 0;  // per-stage mbarrier parity, identical in every thread
+    int seq = 0;         // items taken by this CTA; item seq uses stage seq & 1
+    long long next = 0;
+    if (tid == 0) {
+        s_t = (long long)atomicAdd(prm.ticket, 1ull);
+        if (s_t < prm.total) {
+            const Job &J = job_of(prm, s_t);
+            const Item it = J.items[(s_t - J.tbase) % J.n_items];
+            if (staged_tile(it, cap))
+                tile_issue<F32>(J.A, tile_stage(smem, 0, cap, trows), it.b, it.e, it.k0, it.k1);
+        }
+    }
+    __syncthreads();
     for (;;) {
-        if (tid == 0) s_t = (long long)atomicAdd(prm.ticket, 1ull);
-        __syncthreads();
         const long long t = s_t;
         if (t >= prm.total) break;
-        int ji = 0;
-        while (ji + 1 < prm.njobs && prm.jobs[ji + 1].tbase <= t) ji++;
-        const Job &J = prm.jobs[ji];
+        const Job &J = job_of(prm, t);
         const long long tl = t - J.tbase;
         const int k = (int)(tl / J.n_items);
         const Item it = J.items[tl % J.n_items];
-        // a sticky error (an earlier wait timed out) stops all work of the job
-        if (tid == 0)
-            s_ok = !*(volatile int *)J.err && item_deps(J, it, k, prm.timeout_ns, prm.stall && t == 0);
+        const int cur = seq & 1;
+        if (tid == 0) {
+            next = (long long)atomicAdd(prm.ticket, 1ull);
+            // the matrix is read-only: the next tile's slices are fetched before
+            // its dependencies are even checked
+            if (next < prm.total) {
+                const Job &Jn = job_of(prm, next);
+                const Item itn = Jn.items[(next - Jn.tbase) % Jn.n_items];
+                if (staged_tile(itn, cap))
+                    tile_issue<F32>(Jn.A, tile_stage(smem, cur ^ 1, cap, trows), itn.b, itn.e,
+                                    itn.k0, itn.k1);
+            }
+            s_next = next;
+            // a sticky error (an earlier wait timed out) stops all work of the job
+            s_ok = !*(volatile int *)J.err &&
+                   item_deps(J, it, k, prm.timeout_ns, prm.stall && t == 0);
+        }
         __syncthreads();
-        if (!s_ok) break;
+        if (!s_ok) {
+            // leave no bulk copy in flight: drain the stages issued for t and next
+            if (staged_tile(it, cap)) tile_wait(tile_stage(smem, cur, cap, trows), (phase >> cur) & 1, J.err);
+            const long long nx = s_next;
+            if (nx < prm.total) {
+                const Job &Jn = job_of(prm, nx);
+                if (staged_tile(Jn.items[(nx - Jn.tbase) % Jn.n_items], cap))
+                    tile_wait(tile_stage(smem, cur ^ 1, cap, trows), (phase >> (cur ^ 1)) & 1,
+                              J.err);
+            }
+            break;
+        }
         const double *x = (k == 0) ? J.v : (((J.reps - k) & 1) == 0 ? J.w : J.xtmp);
         double *y = (((J.reps - 1 - k) & 1) == 0) ? J.w : J.xtmp;
         switch (it.kind) {
-        case kGatherJ2:
-            for (int e = it.b + tid; e < it.e; e += 256) J.bll[e] = __ldcg(x + ld_stream_s32(J.bll_j + e));
-            break;
-        case kGatherJ0:
-            for (int e = it.b + tid; e < it.e; e += 256) J.lbuf[e] = __ldcg(x + ld_stream_s32(J.lbuf_j + e));
-            break;
-        case kPack:
-            for (int e = it.b + tid; e < it.e; e += 256) {
-                const uint32_t u = ld_stream_u32(J.pack_src + e);
-                J.gsend[e] = (u & kFromLbuf) ? __ldcg(J.lbuf + (u & ~kFromLbuf)) : __ldcg(x + u);
+        case kGatherJ2: step_gather<true>(J.bll, x, J.bll_j, it.b, it.e, tid); break;
+        case kGatherJ0: step_gather<true>(J.lbuf, x, J.lbuf_j, it.b, it.e, tid); break;
+        case kPack: step_pack<true>(J.gsend, x, J.lbuf, J.pack_src, it.b, it.e, tid); break;
+        case kTransfer: step_transfer<true>(J.grecv, J.gsend, J.xfer_dst, it.b, it.e, tid); break;
+        case kUnpack: step_gather<true>(J.bnl, J.grecv, J.unp_src, it.b, it.e, tid); break;
+        default:
+            if (staged_tile(it, cap)) {
+                const TileStage st = tile_stage(smem, cur, cap, trows);
+                const bool ok = tile_wait(st, (phase >> cur) & 1, J.err);
+                phase ^= 1u << cur;
+                if (ok) tile_compute<V, F32, true>(st, x, J.bll, J.bnl, y, J.scale, it.b, it.e, it.k0, tid);
+            } else {
+                row_direct<F32, true>(J.A, x, J.bll, J.bnl, y, J.scale, it.b, it.e, red, tid);
             }
             break;
-        case kTransfer:
-            for (int e = it.b + tid; e < it.e; e += 256) J.grecv[ld_stream_s32(J.xfer_dst + e)] = __ldcg(J.gsend + e);
-            break;
-        case kUnpack:
-            for (int e = it.b + tid; e < it.e; e += 256) J.bnl[e] = __ldcg(J.grecv + ld_stream_s32(J.unp_src + e));
-            break;
-        default:
-            spmv_rows<V, F32, true>(J.A, x, J.bll, J.bnl, y, J.scale, it.b, it.e, tid, 256);
-            break;
         }
+        seq++;
         __syncthreads();
         if (tid == 0) {
             __threadfence();
             item_signal(J, it);
+            s_t = next;
         }
+        __syncthreads();
     }
 }
 
 // --------------------------------------------------------- phased engine
-__global__ void k_gather2(const double *__restrict__ x, const int32_t *__restrict__ bll_j,
-                          double *__restrict__ bll, int n_bll, const int32_t *__restrict__ lbuf_j,
-                          double *__restrict__ lbuf, int n_lbuf)
+__global__ void __launch_bounds__(NT)
+    k_gather2(const double *x, const int32_t *bll_j, double *bll, int n_bll, const int32_t *lbuf_j,
+              double *lbuf, int n_lbuf)
 {
-    const int total = n_bll + n_lbuf;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        if (e < n_bll)
-            bll[e] = __ldg(x + ld_stream_s32(bll_j + e));
-        else
-            lbuf[e - n_bll] = __ldg(x + ld_stream_s32(lbuf_j + e - n_bll));
+    const int per = NT * 8;
+    for (int b = blockIdx.x * per; b < n_bll + n_lbuf; b += gridDim.x * per) {
+        const int e = min(b + per, n_bll + n_lbuf);
+        if (b < n_bll) step_gather<false>(bll, x, bll_j, b, min(e, n_bll), threadIdx.x);
+        if (e > n_bll) {
+            const int lb = max(b, n_bll) - n_bll, le = e - n_bll;
+            step_gather<false>(lbuf, x, lbuf_j, lb, le, threadIdx.x);
+        }
     }
 }
-__global__ void k_pack(const double *__restrict__ x, const double *__restrict__ lbuf,
-                       const uint32_t *__restrict__ src, double *__restrict__ gsend, int n)
+__global__ void __launch_bounds__(NT)
+    k_pack(const double *x, const double *lbuf, const uint32_t *src, double *gsend, int n)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const uint32_t u = ld_stream_u32(src + e);
-        gsend[e] = (u & kFromLbuf) ? __ldg(lbuf + (u & ~kFromLbuf)) : __ldg(x + u);
-    }
+    const int per = NT * 8;
+    for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
+        step_pack<false>(gsend, x, lbuf, src, b, min(b + per, n), threadIdx.x);
 }
-__global__ void k_transfer(const double *__restrict__ gsend, const int32_t *__restrict__ dst,
-                           double *__restrict__ grecv, int n)
+__global__ void __launch_bounds__(NT)
+    k_transfer(const double *gsend, const int32_t *dst, double *grecv, int n)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-        grecv[ld_stream_s32(dst + e)] = __ldg(gsend + e);
+    const int per = NT * 8;
+    for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
+        step_transfer<false>(grecv, gsend, dst, b, min(b + per, n), threadIdx.x);
 }
-__global__ void k_unpack(const double *__restrict__ grecv, const int32_t *__restrict__ src,
-                         double *__restrict__ bnl, int n)
+__global__ void __launch_bounds__(NT)
+    k_unpack(const double *grecv, const int32_t *src, double *bnl, int n)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-        bnl[e] = __ldg(grecv + ld_stream_s32(src + e));
+    const int per = NT * 8;
+    for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
+        step_gather<false>(bnl, grecv, src, b, min(b + per, n), threadIdx.x);
 }
 template <int V, bool F32>
-__global__ void __launch_bounds__(256) k_spmv(Csr3 A, const double *x, const double *bll,
-                                              const double *bnl, double *y, double scale, int n,
-                                              int rows_per_block)
+__global__ void __launch_bounds__(NT)
+    k_spmv(Csr3 A, const double *x, const double *bll, const double *bnl, double *y, Scale sc,
+           const Item *tiles, int n_tiles, int cap, int trows, int *err)
 {
-    for (int r0 = blockIdx.x * rows_per_block; r0 < n; r0 += gridDim.x * rows_per_block)
-        spmv_rows<V, F32, false>(A, x, bll, bnl, y, scale, r0, min(n, r0 + rows_per_block),
-                                 threadIdx.x, 256);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
+    tile_smem_init(smem);
+    double *red = tile_red(smem, cap, trows);
+    uint32_t phase = 0;
+    int q = blockIdx.x;
+    if (tid == 0 && q < n_tiles) {
+        const Item it = tiles[q];
+        if (staged_tile(it, cap)) tile_issue<F32>(A, tile_stage(smem, 0, cap, trows), it.b, it.e, it.k0, it.k1);
+    }
+    for (int i = 0; q < n_tiles; q += gridDim.x, i++) {
+        const Item it = tiles[q];
+        const int cur = i & 1, qn = q + gridDim.x;
+        if (tid == 0 && qn < n_tiles) {
+            const Item itn = tiles[qn];
+            if (staged_tile(itn, cap))
+                tile_issue<F32>(A, tile_stage(smem, cur ^ 1, cap, trows), itn.b, itn.e, itn.k0, itn.k1);
+        }
+        if (staged_tile(it, cap)) {
+            const TileStage st = tile_stage(smem, cur, cap, trows);
+            const bool ok = tile_wait(st, (phase >> cur) & 1, err);
+            phase ^= 1u << cur;
+            if (ok) tile_compute<V, F32, false>(st, x, bll, bnl, y, sc, it.b, it.e, it.k0, tid);
+        } else {
+            row_direct<F32, false>(A, x, bll, bnl, y, sc, it.b, it.e, red, tid);
+        }
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------- dispatch
@@ -349,7 +717,7 @@ struct FusedKernelTable {
     using Fn = void (*)(const FusedParams<MAXJ>);
     static Fn get(int vec, bool f32)
     {
-#define NAP_CASE(V)                                                   \
+#define NAP_CASE(V) \
     case V: return f32 ? k_fused<V, true, MAXJ> : k_fused<V, false, MAXJ>;
         switch (vec) {
             NAP_CASE(1)
@@ -376,19 +744,28 @@ napspmv_opts resolve_opts(const napspmv_plan_t *P, const napspmv_opts *o)
     if (o->ctas_per_sm) r.ctas_per_sm = o->ctas_per_sm;
     if (o->chunk) r.chunk = o->chunk;
     if (o->tile_rows) r.tile_rows = o->tile_rows;
+    if (o->tile_nnz) r.tile_nnz = o->tile_nnz;
     if (o->timeout_ms) r.timeout_ms = o->timeout_ms;
     r.debug_stall = o->debug_stall;
     return r;
 }
 
-int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows)
+static size_t smem_bytes(int32_t tile_nnz, int32_t tile_rows)
 {
-    if (chunk < 32 || tile_rows < 1) {
-        set_error(NAPSPMV_ERR_ARG, "chunk must be >= 32 and tile_rows >= 1");
+    return (size_t)tile_smem_bytes(tile_nnz, tile_rows);
+}
+
+int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t tile_nnz)
+{
+    if (chunk < 32 || tile_rows < 1 || tile_nnz < 32 ||
+        smem_bytes(tile_nnz, tile_rows) > 200 * 1024) {
+        set_error(NAPSPMV_ERR_ARG, "need chunk >= 32, tile_rows >= 1, tile_nnz >= 32 and "
+                                   "two tile stages (12 B per entry, 4 B per row) within 200 KiB");
         return NAPSPMV_ERR_ARG;
     }
     ItemSet &S = P->items;
-    if (S.d_items && S.chunk == chunk && S.tile_rows == tile_rows) return NAPSPMV_OK;
+    if (S.d_items && S.chunk == chunk && S.tile_rows == tile_rows && S.tile_nnz == tile_nnz)
+        return NAPSPMV_OK;
     const int nn = P->nn;
     std::vector<Item> items;
     std::vector<uint64_t> cnt((size_t)kNumCounters * nn, 0);
@@ -422,9 +799,21 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows)
     for (int x = 0; x < nn; x++)
         for (int64_t b = P->node_bnl[x]; b < P->node_bnl[x + 1]; b += chunk)
             add(kUnpack, x, b, std::min<int64_t>(b + chunk, P->node_bnl[x + 1]), 0, kC4);
-    for (int x = 0; x < nn; x++)
-        for (int64_t b = P->node_rows[x]; b < P->node_rows[x + 1]; b += tile_rows)
-            add(kSpmv, x, b, std::min<int64_t>(b + tile_rows, P->node_rows[x + 1]), 0, kC5);
+    const int32_t spmv_first = (int32_t)items.size();
+    const std::vector<int32_t> &rp = P->h_rowptr;
+    for (int x = 0; x < nn; x++) {
+        int64_t r = P->node_rows[x];
+        const int64_t end = P->node_rows[x + 1];
+        while (r < end) {
+            int64_t e = r;
+            while (e < end && e - r < tile_rows && rp[e + 1] - rp[r] <= tile_nnz) e++;
+            if (e == r) e = r + 1;  // one row longer than the capacity
+            add(kSpmv, x, r, e, 0, kC5);
+            items.back().k0 = rp[r];
+            items.back().k1 = rp[e];
+            r = e;
+        }
+    }
 
     Item *d_items = nullptr;
     uint64_t *d_cnt = nullptr;
@@ -437,8 +826,10 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows)
     S.d_items = d_items;
     S.d_cnt = d_cnt;
     S.n_items = (int32_t)items.size();
+    S.spmv_first = spmv_first;
     S.chunk = chunk;
     S.tile_rows = tile_rows;
+    S.tile_nnz = tile_nnz;
     return NAPSPMV_OK;
 }
 
@@ -476,6 +867,14 @@ void ws_free(napspmv_ws_t *ws)
     ws->err = nullptr;
 }
 
+static Scale make_scale(double s)
+{
+    Scale sc{s, kNoPow2};
+    int e = 0;
+    if (s != 0.0 && std::isfinite(s) && std::frexp(s, &e) == 0.5 && s > 0) sc.e2 = e - 1;
+    return sc;
+}
+
 static Job make_job(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
                     double scale, bool f32)
 {
@@ -483,7 +882,7 @@ static Job make_job(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double
     J.items = P->items.d_items;
     J.n_items = P->items.n_items;
     J.reps = reps;
-    J.scale = scale;
+    J.scale = make_scale(scale);
     J.A = Csr3{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
     J.bll_j = P->lists[L_BLL].d_idx;
     J.lbuf_j = P->lists[L_LBUF].d_idx;
@@ -507,6 +906,14 @@ static Job make_job(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double
     return J;
 }
 
+template <class Fn>
+static int prepare_smem(Fn fn, size_t bytes)
+{
+    if (bytes > 48 * 1024)
+        NAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return NAPSPMV_OK;
+}
+
 template <int MAXJ>
 static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *const *ws,
                         const double *const *v, double *const *w, const int32_t *reps,
@@ -517,6 +924,8 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
     prm.njobs = count;
     prm.stall = o.debug_stall ? 1 : 0;
     prm.timeout_ns = (long long)o.timeout_ms * 1000000ll;
+    prm.cap = o.tile_nnz;
+    prm.tile_rows = o.tile_rows;
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
     long long total = 0;
     for (int i = 0; i < count; i++) {
@@ -529,12 +938,14 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
     prm.total = total;
     prm.ticket = prm.jobs[0].ctr;
     auto fn = FusedKernelTable<MAXJ>::get(o.vec, f32);
+    const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows);
+    if (int rc = prepare_smem(fn, sm)) return rc;
     int occ = 0;
-    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, 0));
+    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, sm));
     int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
     long long grid = (long long)plans[0]->num_sms * per_sm;
     grid = std::max(1ll, std::min(grid, total));
-    fn<<<(int)grid, 256, 0, s>>>(prm);
+    fn<<<(int)grid, NT, sm, s>>>(prm);
     NAP_CUDA(cudaGetLastError());
     count_launch(1);
     return NAPSPMV_OK;
@@ -544,13 +955,13 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
                          double scale, const napspmv_opts &o, cudaStream_t s)
 {
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
-    const int T = 256;
     auto grid = [&](int64_t n) {
-        return (int)std::max<int64_t>(1, std::min<int64_t>((n + T - 1) / T, (int64_t)P->num_sms * 8));
+        return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
+                                                            (int64_t)P->num_sms * 8));
     };
     Csr3 A{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
-    using SpmvFn = void (*)(Csr3, const double *, const double *, const double *, double *, double,
-                            int, int);
+    using SpmvFn = void (*)(Csr3, const double *, const double *, const double *, double *, Scale,
+                            const Item *, int, int, int, int *);
     SpmvFn sp = nullptr;
 #define NAP_CASE(V) \
     case V: sp = f32 ? k_spmv<V, true> : k_spmv<V, false>; break;
@@ -563,28 +974,32 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
         NAP_CASE(32)
     }
 #undef NAP_CASE
-    const int rows_per_block = 256 / o.vec * 4;
+    const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows);
+    if (int rc = prepare_smem(sp, sm)) return rc;
+    const ItemSet &S = P->items;
+    const int n_tiles = S.n_items - S.spmv_first;
     for (int k = 0; k < reps; k++) {
         const double *x = (k == 0) ? v : (((reps - k) & 1) == 0 ? w : ws->xtmp);
         double *y = (((reps - 1 - k) & 1) == 0) ? w : ws->xtmp;
         if (P->n_bll + P->n_lbuf > 0) {
-            k_gather2<<<grid(P->n_bll + P->n_lbuf), T, 0, s>>>(x, P->lists[L_BLL].d_idx, ws->bll,
-                                                               (int)P->n_bll, P->lists[L_LBUF].d_idx,
-                                                               ws->lbuf, (int)P->n_lbuf);
+            k_gather2<<<grid(P->n_bll + P->n_lbuf), NT, 0, s>>>(
+                x, P->lists[L_BLL].d_idx, ws->bll, (int)P->n_bll, P->lists[L_LBUF].d_idx, ws->lbuf,
+                (int)P->n_lbuf);
             count_launch(1);
         }
         if (P->n_gs > 0) {
-            k_pack<<<grid(P->n_gs), T, 0, s>>>(x, ws->lbuf, P->d_pack_src, ws->gsend, (int)P->n_gs);
-            k_transfer<<<grid(P->n_gs), T, 0, s>>>(ws->gsend, P->d_xfer_dst, ws->grecv, (int)P->n_gs);
+            k_pack<<<grid(P->n_gs), NT, 0, s>>>(x, ws->lbuf, P->d_pack_src, ws->gsend, (int)P->n_gs);
+            k_transfer<<<grid(P->n_gs), NT, 0, s>>>(ws->gsend, P->d_xfer_dst, ws->grecv,
+                                                    (int)P->n_gs);
             count_launch(2);
         }
         if (P->n_bnl > 0) {
-            k_unpack<<<grid(P->n_bnl), T, 0, s>>>(ws->grecv, P->d_unp_src, ws->bnl, (int)P->n_bnl);
+            k_unpack<<<grid(P->n_bnl), NT, 0, s>>>(ws->grecv, P->d_unp_src, ws->bnl, (int)P->n_bnl);
             count_launch(1);
         }
-        const int64_t nb = (P->n + rows_per_block - 1) / rows_per_block;
-        sp<<<(int)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)P->num_sms * 16)), T, 0, s>>>(
-            A, x, ws->bll, ws->bnl, y, scale, (int)P->n, rows_per_block);
+        sp<<<std::max(1, std::min(n_tiles, P->num_sms * 4)), NT, sm, s>>>(
+            A, x, ws->bll, ws->bnl, y, make_scale(scale), S.d_items + S.spmv_first, n_tiles,
+            o.tile_nnz, o.tile_rows, ws->err);
         count_launch(1);
         NAP_CUDA(cudaGetLastError());
     }
@@ -630,46 +1045,47 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
         return NAPSPMV_ERR_ARG;
     }
     napspmv_opts o = resolve_opts(P0, opts);
-    for (int i = 0; i < count; i++) {
+    int cur = 0;
+    NAP_CUDA(cudaGetDevice(&cur));
+    if (cur != P0->device) NAP_CUDA(cudaSetDevice(P0->device));
+    int rc = NAPSPMV_OK;
+    for (int i = 0; i < count && !rc; i++) {
         napspmv_plan_t *P = plans[i];
         if (!P || !v[i] || !w[i] || reps[i] < 1 || (const double *)w[i] == v[i]) {
             set_error(NAPSPMV_ERR_ARG, "NULL plan or vector, reps < 1, or w == v");
-            return NAPSPMV_ERR_ARG;
+            rc = NAPSPMV_ERR_ARG;
+            break;
         }
         if (P->device != P0->device) {
             set_error(NAPSPMV_ERR_ARG, "all plans of a batch must live on one device");
-            return NAPSPMV_ERR_ARG;
+            rc = NAPSPMV_ERR_ARG;
+            break;
         }
-        int rc = check_opts(P, o);
-        if (rc) return rc;
-        if (count > 1 || o.engine == NAPSPMV_ENGINE_FUSED) {
-            rc = build_items(P, o.chunk, o.tile_rows);
-            if (rc) return rc;
-        }
+        if ((rc = check_opts(P, o))) break;
+        if ((rc = build_items(P, o.chunk, o.tile_rows, o.tile_nnz))) break;
         for (int q = 0; q < i; q++) {
             napspmv_ws_t *a = ws && ws[i] ? ws[i] : P->ws;
             napspmv_ws_t *b = ws && ws[q] ? ws[q] : plans[q]->ws;
             if (a == b) {
                 set_error(NAPSPMV_ERR_ARG, "two batch entries share one workspace");
-                return NAPSPMV_ERR_ARG;
+                rc = NAPSPMV_ERR_ARG;
+                break;
             }
         }
-        if (ws && ws[i] && ws[i]->plan != P) {
+        if (!rc && ws && ws[i] && ws[i]->plan != P) {
             set_error(NAPSPMV_ERR_ARG, "workspace belongs to another plan");
-            return NAPSPMV_ERR_ARG;
+            rc = NAPSPMV_ERR_ARG;
         }
     }
-    int cur = 0;
-    NAP_CUDA(cudaGetDevice(&cur));
-    if (cur != P0->device) NAP_CUDA(cudaSetDevice(P0->device));
-    int rc;
-    if (count == 1 && o.engine == NAPSPMV_ENGINE_PHASED)
-        rc = launch_phased(P0, ws && ws[0] ? ws[0] : P0->ws, v[0], w[0], reps[0],
-                           scale ? scale[0] : 1.0, o, s);
-    else if (count == 1)
-        rc = launch_fused<1>(count, plans, ws, v, w, reps, scale, o, s);
-    else
-        rc = launch_fused<64>(count, plans, ws, v, w, reps, scale, o, s);
+    if (!rc) {
+        if (count == 1 && o.engine == NAPSPMV_ENGINE_PHASED)
+            rc = launch_phased(P0, ws && ws[0] ? ws[0] : P0->ws, v[0], w[0], reps[0],
+                               scale ? scale[0] : 1.0, o, s);
+        else if (count == 1)
+            rc = launch_fused<1>(count, plans, ws, v, w, reps, scale, o, s);
+        else
+            rc = launch_fused<64>(count, plans, ws, v, w, reps, scale, o, s);
+    }
     if (cur != P0->device) cudaSetDevice(cur);
     return rc;
 }

@@ -54,12 +54,14 @@ struct Item {
     int32_t node;  // node whose data the item touches (sender node for kTransfer)
     int32_t b, e;  // element (or row) range
     int32_t msg;   // kTransfer: first g_send message overlapping [b, e)
-    int32_t pad[3];
+    int32_t k0, k1;  // kSpmv: stored-entry range [row_ptr[b], row_ptr[e])
+    int32_t pad;
 };
 
 struct ItemSet {
-    int32_t chunk = 0, tile_rows = 0;
+    int32_t chunk = 0, tile_rows = 0, tile_nnz = 0;
     int32_t n_items = 0;
+    int32_t spmv_first = 0;  // items [spmv_first, n_items) are the row tiles
     Item *d_items = nullptr;
     // per-apply increments of every counter, [kNumCounters][nn]
     uint64_t *d_cnt = nullptr;
@@ -114,6 +116,7 @@ struct napspmv_plan_s {
 
     // per-node ranges (host) used to cut work items
     std::vector<int64_t> node_bll, node_lbuf, node_gs, node_bnl, node_rows;  // [nn+1]
+    std::vector<int32_t> h_rowptr;         // host copy of the row pointer, for tiling
     std::vector<int64_t> gs_msg_off;       // [n_inter + 1] g_send offsets in INTER order
     std::vector<int32_t> gs_msg_dstnode;   // [n_inter]
     int32_t *d_gs_msg_off = nullptr;       // device copies
@@ -126,7 +129,7 @@ struct napspmv_plan_s {
 };
 
 namespace nap {
-int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows);
+int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t tile_nnz);
 int ws_alloc(napspmv_plan_t *P, napspmv_ws_t *ws);
 void ws_free(napspmv_ws_t *ws);
 void plan_free(napspmv_plan_t *P);

@@ -808,7 +808,9 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
     bnl_keys.alloc(0);
 
     // ---- three-block CSR
-    CK(cudaMalloc(&P->d_rowptr, sizeof(int32_t) * (n + 1)));
+    // padded so that 16-byte bulk copies of a row range may read past the end
+    CK(cudaMalloc(&P->d_rowptr, sizeof(int32_t) * (n + 16)));
+    CK(cudaMemset(P->d_rowptr, 0, sizeof(int32_t) * (n + 16)));
     CK(cudaMalloc(&P->d_colenc, sizeof(uint32_t) * std::max<int64_t>(nnz, 1) + 64));
     CK(cudaMalloc(&P->d_val, sizeof(double) * std::max<int64_t>(nnz, 1) + 64));
     CK(cudaMalloc(&P->d_split, sizeof(int32_t) * 3 * n));
@@ -842,6 +844,12 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
             while (i < M && msg_src[i] < first_rank) i++;
             P->node_gs[x] = gs_off[i];
         }
+    }
+    {
+        std::vector<int64_t> h(n + 1);
+        CK(cudaMemcpy(h.data(), rp.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+        P->h_rowptr.resize(n + 1);
+        for (int64_t i = 0; i <= n; i++) P->h_rowptr[i] = (int32_t)h[i];
     }
     P->gs_msg_off = gs_off;
     P->gs_msg_dstnode = msg_dstnode;
@@ -914,16 +922,19 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         P->ws->owned_by_plan = true;
         // defaults: lanes per row from the mean row length
         double avg = (double)P->nnz / (double)P->n;
-        int vec = avg <= 2.5 ? 1 : avg <= 5 ? 2 : avg <= 12 ? 4 : avg <= 24 ? 8 : avg <= 48 ? 16 : 32;
+        // rows are summed from shared memory; one lane per row keeps exactly one
+        // FP64 FMA per stored entry (GB300's FP64 pipe is the scarce unit)
+        int vec = avg <= 48 ? 1 : avg <= 192 ? 8 : 32;
         P->defaults.precision = NAPSPMV_PREC_F64;
         P->defaults.engine = NAPSPMV_ENGINE_FUSED;
         P->defaults.vec = vec;
         P->defaults.ctas_per_sm = 0;  // occupancy maximum
         P->defaults.chunk = 4096;
-        P->defaults.tile_rows = 1024;
+        P->defaults.tile_rows = 512;
+        P->defaults.tile_nnz = 2048;
         P->defaults.timeout_ms = 10000;
         P->defaults.debug_stall = 0;
-        rc = build_items(P, P->defaults.chunk, P->defaults.tile_rows);
+        rc = build_items(P, P->defaults.chunk, P->defaults.tile_rows, P->defaults.tile_nnz);
         if (rc) throw NapError{rc, "work-item construction failed"};
     } catch (const NapError &e) {
         plan_free(P);

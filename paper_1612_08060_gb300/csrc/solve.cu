@@ -8,6 +8,7 @@
 // its value does not depend on scheduling.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "internal.h"
 
@@ -232,7 +233,7 @@ extern "C" {
 
 int napspmv_dot(const double *x, const double *y, int64_t n, double *result, void *stream)
 {
-    if (!x || !y || !result || n < 0) {
+    if ((n > 0 && (!x || !y)) || !result || n < 0) {
         set_error(NAPSPMV_ERR_ARG, "NULL vector or result, or n < 0");
         return NAPSPMV_ERR_ARG;
     }
@@ -315,3 +316,256 @@ int napspmv_cg_ir(napspmv_plan_t *P, const double *b, double *x, double rtol, do
 }
 
 }  // extern "C"
+
+// ===================================================================
+// Batched CG steps over independent requests (the request server).
+//
+// Every slot is one CG solve with its own plan, vectors and scalars.  A dot
+// product of slot i always uses kSlotBlocks blocks over a fixed strided
+// partition of its own vectors and a fixed-order final sum, so its value
+// does not depend on which other slots share the launch.
+namespace nap {
+namespace {
+
+constexpr int kMaxSlots = 64;
+constexpr int kSlotBlocks = 64;
+
+enum Scl { S_RR = 0, S_PQ = 1, S_ALPHA = 2, S_BETA = 3, S_RRNEW = 4, S_BB = 5 };
+
+struct SlotVecs {
+    int32_t count;
+    int64_t n[kMaxSlots];
+    const double *b[kMaxSlots];
+    double *x[kMaxSlots], *r[kMaxSlots], *p[kMaxSlots], *q[kMaxSlots], *scal[kMaxSlots];
+};
+
+__device__ __forceinline__ double block_sum_any(double v, double *sh)
+{
+    return block_sum(v, sh);
+}
+
+// mode 0: r = b - q, p = r, partial(r.r) and partial(b.b)
+// mode 1: partial(p.q)
+// mode 2: x += alpha p, r -= alpha q, partial(r.r)
+// mode 3: p = r + beta p
+// mode 4: r = b, p = b, partial(r.r), partial(b.b)   (x = 0)
+__global__ void __launch_bounds__(kThreads) k_slot_vec(const __grid_constant__ SlotVecs S, int mode,
+                                                       double *partial)
+{
+    __shared__ double sh[kThreads / 32];
+    const int i = blockIdx.y;
+    const int64_t n = S.n[i];
+    const double *b = S.b[i];
+    double *x = S.x[i], *r = S.r[i], *p = S.p[i], *q = S.q[i];
+    const double alpha = mode == 2 ? S.scal[i][S_ALPHA] : 0.0;
+    const double beta = mode == 3 ? S.scal[i][S_BETA] : 0.0;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < n;
+         k += (int64_t)kSlotBlocks * kThreads) {
+        if (mode == 0 || mode == 4) {
+            const double v = mode == 0 ? b[k] - q[k] : b[k];
+            r[k] = v;
+            p[k] = v;
+            if (mode == 4) x[k] = 0.0;
+            s1 = fma(v, v, s1);
+            s2 = fma(b[k], b[k], s2);
+        } else if (mode == 1) {
+            s1 = fma(p[k], q[k], s1);
+        } else if (mode == 2) {
+            x[k] = fma(alpha, p[k], x[k]);
+            const double v = fma(-alpha, q[k], r[k]);
+            r[k] = v;
+            s1 = fma(v, v, s1);
+        } else {
+            p[k] = fma(beta, p[k], r[k]);
+        }
+    }
+    if (mode == 3) return;
+    s1 = block_sum_any(s1, sh);
+    if (mode == 0 || mode == 4) s2 = block_sum_any(s2, sh);
+    if (threadIdx.x == 0) {
+        partial[(i * kSlotBlocks + blockIdx.x) * 2 + 0] = s1;
+        partial[(i * kSlotBlocks + blockIdx.x) * 2 + 1] = s2;
+    }
+}
+
+// Fixed-order sums of the partials and the scalar recurrences of CG.
+__global__ void k_slot_final(const __grid_constant__ SlotVecs S, int mode, const double *partial)
+{
+    const int i = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    double a = 0.0, c = 0.0;
+    for (int q = 0; q < kSlotBlocks; q++) {
+        a += partial[(i * kSlotBlocks + q) * 2 + 0];
+        c += partial[(i * kSlotBlocks + q) * 2 + 1];
+    }
+    double *s = S.scal[i];
+    if (mode == 0 || mode == 4) {
+        s[S_RR] = a;
+        s[S_BB] = c;
+    } else if (mode == 1) {
+        s[S_PQ] = a;
+        s[S_ALPHA] = s[S_RR] / a;
+    } else if (mode == 2) {
+        s[S_RRNEW] = a;
+        s[S_BETA] = a / s[S_RR];
+        s[S_RR] = a;
+    }
+}
+
+int slot_vec(const SlotVecs &S, int mode, double *partial, cudaStream_t st)
+{
+    k_slot_vec<<<dim3(kSlotBlocks, S.count), kThreads, 0, st>>>(S, mode, partial);
+    count_launch(1);
+    if (mode != 3) {
+        k_slot_final<<<S.count, 32, 0, st>>>(S, mode, partial);
+        count_launch(1);
+    }
+    NAP_CUDA(cudaGetLastError());
+    return NAPSPMV_OK;
+}
+
+int slot_setup(int32_t count, const napspmv_cg_slot *slots, SlotVecs &S)
+{
+    if (count < 1 || count > kMaxSlots || !slots) {
+        set_error(NAPSPMV_ERR_ARG, "need 1..64 CG slots");
+        return NAPSPMV_ERR_ARG;
+    }
+    memset(&S, 0, sizeof(S));
+    S.count = count;
+    for (int i = 0; i < count; i++) {
+        const napspmv_cg_slot &c = slots[i];
+        if (!c.plan || !c.b || !c.x || !c.r || !c.p || !c.q || !c.scal) {
+            set_error(NAPSPMV_ERR_ARG, "CG slot with a NULL pointer");
+            return NAPSPMV_ERR_ARG;
+        }
+        S.n[i] = c.plan->n;
+        S.b[i] = c.b;
+        S.x[i] = c.x;
+        S.r[i] = c.r;
+        S.p[i] = c.p;
+        S.q[i] = c.q;
+        S.scal[i] = c.scal;
+    }
+    return NAPSPMV_OK;
+}
+
+int slot_apply(int32_t count, const napspmv_cg_slot *slots, bool from_x, int32_t precision,
+               cudaStream_t st)
+{
+    napspmv_plan_t *plans[kMaxSlots];
+    napspmv_ws_t *wss[kMaxSlots];
+    const double *vs[kMaxSlots];
+    double *ws_[kMaxSlots];
+    int32_t reps[kMaxSlots];
+    double sc[kMaxSlots];
+    for (int i = 0; i < count; i++) {
+        plans[i] = slots[i].plan;
+        wss[i] = slots[i].ws;
+        vs[i] = from_x ? slots[i].x : slots[i].p;
+        ws_[i] = slots[i].q;
+        reps[i] = 1;
+        sc[i] = 1.0;
+    }
+    napspmv_opts o = plans[0]->defaults;
+    o.precision = precision;
+    o.engine = NAPSPMV_ENGINE_FUSED;
+    return apply_batch(count, plans, wss, vs, ws_, reps, sc, &o, st);
+}
+
+struct Partials {
+    double *p = nullptr;
+    cudaStream_t s = 0;
+    ~Partials()
+    {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+}  // namespace
+}  // namespace nap
+
+extern "C" {
+
+int napspmv_cg_batch_init(int32_t count, const napspmv_cg_slot *slots, int32_t precision,
+                          int32_t x_is_zero, void *stream)
+{
+    SlotVecs S;
+    int rc = slot_setup(count, slots, S);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Partials P;
+    P.s = st;
+    NAP_CUDA(cudaMallocAsync(&P.p, sizeof(double) * 2 * kSlotBlocks * count, st));
+    if (x_is_zero) return slot_vec(S, 4, P.p, st);
+    if ((rc = slot_apply(count, slots, true, precision, st))) return rc;
+    return slot_vec(S, 0, P.p, st);
+}
+
+int napspmv_cg_batch_iterate(int32_t count, const napspmv_cg_slot *slots, int32_t precision,
+                             int32_t iters, void *stream)
+{
+    SlotVecs S;
+    int rc = slot_setup(count, slots, S);
+    if (rc) return rc;
+    if (iters < 0) {
+        set_error(NAPSPMV_ERR_ARG, "iters < 0");
+        return NAPSPMV_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Partials P;
+    P.s = st;
+    NAP_CUDA(cudaMallocAsync(&P.p, sizeof(double) * 2 * kSlotBlocks * count, st));
+    for (int it = 0; it < iters; it++) {
+        if ((rc = slot_apply(count, slots, false, precision, st))) return rc;
+        if ((rc = slot_vec(S, 1, P.p, st))) return rc;
+        if ((rc = slot_vec(S, 2, P.p, st))) return rc;
+        if ((rc = slot_vec(S, 3, P.p, st))) return rc;
+    }
+    return NAPSPMV_OK;
+}
+
+}  // extern "C"
+
+namespace nap {
+namespace {
+struct AddVecs {
+    int32_t count;
+    int64_t n[kMaxSlots];
+    double *y[kMaxSlots];
+    const double *x[kMaxSlots];
+};
+__global__ void k_slot_add(const __grid_constant__ AddVecs A)
+{
+    const int i = blockIdx.y;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < A.n[i];
+         k += (int64_t)gridDim.x * blockDim.x)
+        A.y[i][k] += A.x[i][k];
+}
+}  // namespace
+}  // namespace nap
+
+extern "C" int napspmv_batch_add(int32_t count, double *const *y, const double *const *x,
+                                 const int64_t *n, void *stream)
+{
+    if (count < 1 || count > kMaxSlots || !y || !x || !n) {
+        set_error(NAPSPMV_ERR_ARG, "need 1..64 vector pairs");
+        return NAPSPMV_ERR_ARG;
+    }
+    AddVecs A;
+    memset(&A, 0, sizeof(A));
+    A.count = count;
+    for (int i = 0; i < count; i++) {
+        if (!y[i] || !x[i] || n[i] < 0) {
+            set_error(NAPSPMV_ERR_ARG, "NULL vector or n < 0");
+            return NAPSPMV_ERR_ARG;
+        }
+        A.y[i] = y[i];
+        A.x[i] = x[i];
+        A.n[i] = n[i];
+    }
+    k_slot_add<<<dim3(kSlotBlocks, count), kThreads, 0, (cudaStream_t)stream>>>(A);
+    count_launch(1);
+    NAP_CUDA(cudaGetLastError());
+    return NAPSPMV_OK;
+}

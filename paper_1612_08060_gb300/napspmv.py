@@ -38,7 +38,7 @@ class napspmv_csr(C.Structure):
 class napspmv_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("engine", C.c_int32), ("vec", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("chunk", C.c_int32), ("tile_rows", C.c_int32),
-                ("timeout_ms", C.c_int32), ("debug_stall", C.c_int32)]
+                ("tile_nnz", C.c_int32), ("timeout_ms", C.c_int32), ("debug_stall", C.c_int32)]
 
 
 STAT_FIELDS = [
@@ -56,6 +56,11 @@ class napspmv_stats(C.Structure):
     _fields_ = [(f, C.c_int64) for f in STAT_FIELDS] + [
         ("bytes_csr_f64", C.c_double), ("bytes_csr_f32", C.c_double), ("bytes_msg", C.c_double),
         ("plan_ms", C.c_double)]
+
+
+class napspmv_cg_slot(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("ws", C.c_void_p), ("b", C.c_void_p), ("x", C.c_void_p),
+                ("r", C.c_void_p), ("p", C.c_void_p), ("q", C.c_void_p), ("scal", C.c_void_p)]
 
 
 class napspmv_cg_info(C.Structure):
@@ -100,6 +105,12 @@ def lib():
             "napspmv_cg": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_int32,
                                      C.POINTER(napspmv_cg_info), _VP]),
             "napspmv_dot": (C.c_int, [_VP, _VP, C.c_int64, _VP, _VP]),
+            "napspmv_cg_batch_init": (C.c_int, [C.c_int32, C.POINTER(napspmv_cg_slot), C.c_int32,
+                                                C.c_int32, _VP]),
+            "napspmv_cg_batch_iterate": (C.c_int, [C.c_int32, C.POINTER(napspmv_cg_slot),
+                                                   C.c_int32, C.c_int32, _VP]),
+            "napspmv_batch_add": (C.c_int, [C.c_int32, C.POINTER(_VP), C.POINTER(_VP),
+                                            C.POINTER(C.c_int64), _VP]),
             "napspmv_plan_destroy": (None, [_VP]),
             "napspmv_strerror": (C.c_char_p, [C.c_int]),
             "napspmv_last_error": (C.c_char_p, []),
@@ -313,3 +324,33 @@ def napspmv_strerror(code):
 
 def napspmv_launch_count():
     return int(lib().napspmv_launch_count())
+
+
+def _slots(slots):
+    arr = (napspmv_cg_slot * len(slots))()
+    for i, d in enumerate(slots):
+        arr[i] = napspmv_cg_slot(d["plan"].handle, d["ws"].handle if d.get("ws") else None,
+                                 _dptr(d["b"]), _dptr(d["x"]), _dptr(d["r"]), _dptr(d["p"]),
+                                 _dptr(d["q"]), _dptr(d["scal"]))
+    return arr
+
+
+def napspmv_cg_batch_init(slots, precision=PREC_F64, x_is_zero=False, stream=None):
+    """slots: list of dicts with plan, ws, b, x, r, p, q, scal (tensors)."""
+    arr = _slots(slots)
+    _check(lib().napspmv_cg_batch_init(len(slots), arr, int(precision), int(bool(x_is_zero)),
+                                       _stream(stream)))
+
+
+def napspmv_cg_batch_iterate(slots, precision=PREC_F64, iters=1, stream=None):
+    arr = _slots(slots)
+    _check(lib().napspmv_cg_batch_iterate(len(slots), arr, int(precision), int(iters),
+                                          _stream(stream)))
+
+
+def napspmv_batch_add(ys, xs, stream=None):
+    n = len(ys)
+    Y = (_VP * n)(*[_dptr(y) for y in ys])
+    X = (_VP * n)(*[_dptr(x) for x in xs])
+    N = (C.c_int64 * n)(*[int(y.numel()) for y in ys])
+    _check(lib().napspmv_batch_add(n, Y, X, N, _stream(stream)))

@@ -1,0 +1,250 @@
+"""Continuous-batching request server for node-aware SpMV and CG-IR solves.
+
+Requests (an SpMV, or a CG solve to ||b - A x|| <= rtol ||b|| with FP32-stored
+values inside FP64 iterative refinement) arrive over time on Poisson matrices of
+differing size.  The server:
+
+* admits an arrived request when a slot is free (at most ``max_active`` in
+  flight) and its device memory fits the budget; plans (built on first use) stay
+  resident in an LRU cache, evicted only when unused and memory is short;
+* every step launches one batched fused apply for all SpMV requests, one batched
+  CG-residual step (FP64 values) for the solves entering an outer iteration, and
+  ``iters_per_step`` batched CG iterations (FP32 values) for the solves in their
+  inner loop, so the work of all admitted requests overlaps on the device;
+* reads every solve's scalars with one device-to-host copy per step, retires
+  finished requests and stamps their latency (completion - arrival).
+
+Each request's arithmetic is independent of what else is in flight (fixed
+per-row and per-slot reduction orders), so a request served alone and in a mix
+gives the same bits.  ``max_active=1`` is the plain per-request loop (same
+kernels, same plan cache, one request at a time in arrival order).
+
+PyTorch provides device memory and the stream; all compute is in libnapspmv.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import inputs
+from . import napspmv as nap
+
+
+class Matrix:
+    def __init__(self, key, A, n_p, ppn):
+        t0 = time.perf_counter()
+        self.key = key
+        self.n = A.n
+        self.plan = nap.napspmv_plan(A.row_ptr, A.col, A.val, n_p, ppn, nap.F32_VALUES)
+        self.build_s = time.perf_counter() - t0
+        st = nap.napspmv_plan_stats(self.plan)
+        bufs = st["bll_total"] + st["lbuf_total"] + 2 * st["nap_inter_vals"] + st["bnl_total"]
+        # matrix (col, values FP64 + FP32, row pointer) + index arrays + one workspace
+        self.plan_bytes = A.nnz * 16 + A.n * 12 + bufs * 12 + 8 * A.n
+        self.ws_bytes = bufs * 8 + A.n * 8
+        self.users = 0
+
+
+class Request:
+    def __init__(self, spec):
+        self.spec = spec
+        self.id = spec["id"]
+        self.arrival = spec["arrival"]
+        self.kind = spec["kind"]
+        self.state = "queued"
+        self.t_done = None
+        self.outer = 0
+        self.inner = 0
+        self.result = None
+
+
+class Server:
+    def __init__(self, mem_budget=None, max_active=64, iters_per_step=8, rtol=1e-10,
+                 inner_rtol=1e-4, max_outer=40, max_inner=200000, device=None, keep_results=False):
+        self.dev = torch.device(device or "cuda")
+        free, _ = torch.cuda.mem_get_info(self.dev)
+        self.budget = int(mem_budget if mem_budget else 0.5 * free)
+        self.max_active = max_active
+        self.iters = iters_per_step
+        self.rtol, self.inner_rtol = rtol, inner_rtol
+        self.max_outer, self.max_inner = max_outer, max_inner
+        self.keep = keep_results
+        self.stream = torch.cuda.Stream(self.dev)
+        self.cache: "collections.OrderedDict[str, Matrix]" = collections.OrderedDict()
+        self.mem_used = 0
+        self.steps = 0
+        self.batch_sizes = []
+
+    # ------------------------------------------------------------ matrices
+    def _matrix(self, spec):
+        key = f"{spec['dim']}d_{spec['side']}_np{spec['n_p']}_ppn{spec['ppn']}"
+        if key in self.cache:
+            self.cache.move_to_end(key)
+            return self.cache[key]
+        A = inputs.poisson2d(spec["side"]) if spec["dim"] == 2 else inputs.poisson3d(spec["side"])
+        with torch.cuda.stream(self.stream):
+            m = Matrix(key, A, spec["n_p"], spec["ppn"])
+        self.cache[key] = m
+        self.mem_used += m.plan_bytes
+        return m
+
+    def _evict(self, need):
+        for key in list(self.cache):
+            if self.mem_used + need <= self.budget:
+                return
+            m = self.cache[key]
+            if m.users == 0:
+                self.mem_used -= m.plan_bytes
+                del self.cache[key]
+
+    def _request_bytes(self, spec, m):
+        vecs = 2 if spec["kind"] == "spmv" else 9
+        return vecs * 8 * m.n + m.ws_bytes
+
+    # ------------------------------------------------------------ admission
+    def _admit(self, r):
+        spec = r.spec
+        m = self._matrix(spec)
+        need = self._request_bytes(spec, m)
+        if self.mem_used + need > self.budget:
+            self._evict(need)
+            if self.mem_used + need > self.budget:
+                return False
+        r.m = m
+        m.users += 1
+        r.bytes = need
+        self.mem_used += need
+        n = m.n
+        d = self.dev
+        with torch.cuda.stream(self.stream):
+            r.ws = nap.Workspace(m.plan)
+            rhs = torch.from_numpy(inputs.vector(n, spec["seed"])).to(d, non_blocking=True)
+            if r.kind == "spmv":
+                r.v = rhs
+                r.w = torch.empty(n, dtype=torch.float64, device=d)
+                r.state = "spmv"
+            else:
+                r.b = rhs
+                z = lambda: torch.zeros(n, dtype=torch.float64, device=d)  # noqa: E731
+                r.x, r.ro, r.po, r.qo = z(), z(), z(), z()
+                r.d, r.ri, r.pi, r.qi = z(), z(), z(), z()
+                r.scal = torch.zeros(2, 8, dtype=torch.float64, device=d)
+                r.outer_slot = dict(plan=m.plan, ws=r.ws, b=r.b, x=r.x, r=r.ro, p=r.po, q=r.qo,
+                                    scal=r.scal[0])
+                r.inner_slot = dict(plan=m.plan, ws=r.ws, b=r.ro, x=r.d, r=r.ri, p=r.pi, q=r.qi,
+                                    scal=r.scal[1])
+                r.state = "outer"
+        return True
+
+    def _retire(self, r, now):
+        r.t_done = now
+        r.state = "done"
+        if self.keep:
+            r.result = (r.w if r.kind == "spmv" else r.x).cpu().numpy()
+        r.m.users -= 1
+        self.mem_used -= r.bytes
+        for a in ("ws", "v", "w", "b", "x", "ro", "po", "qo", "d", "ri", "pi", "qi", "scal",
+                  "outer_slot", "inner_slot"):
+            if hasattr(r, a):
+                delattr(r, a)
+
+    # ------------------------------------------------------------ one step
+    @staticmethod
+    def _chunks(xs, k=64):
+        return [xs[i:i + k] for i in range(0, len(xs), k)]
+
+    def _step(self, active):
+        s = self.stream
+        spmv = [r for r in active if r.state == "spmv"]
+        outer = [r for r in active if r.state == "outer"]
+        inner = [r for r in active if r.state == "inner"]
+        self.batch_sizes.append(len(active))
+        with torch.cuda.stream(s):
+            for grp in self._chunks(spmv):
+                nap.napspmv_apply_batch([r.m.plan for r in grp], [r.v for r in grp],
+                                        [r.w for r in grp], [1] * len(grp),
+                                        ws=[r.ws for r in grp], stream=s)
+            for grp in self._chunks(outer):
+                nap.napspmv_cg_batch_init([r.outer_slot for r in grp], nap.PREC_F64, stream=s)
+            for grp in self._chunks(inner):
+                nap.napspmv_cg_batch_iterate([r.inner_slot for r in grp], nap.PREC_F32,
+                                             self.iters, stream=s)
+            cg = outer + inner
+            host = None
+            if cg:
+                host = torch.stack([r.scal for r in cg]).cpu().numpy()  # one copy, synchronises
+            else:
+                s.synchronize()
+        now = time.perf_counter()
+        for r in spmv:
+            self._retire(r, now)
+        to_inner, to_outer = [], []
+        for q, r in enumerate(cg):
+            sc = host[q]
+            if r.state == "outer":
+                rel = math.sqrt(max(sc[0][0], 0.0)) / math.sqrt(max(sc[0][5], 1e-300))
+                r.relres = rel
+                if rel <= self.rtol or r.outer >= self.max_outer or not math.isfinite(rel):
+                    self._retire(r, now)
+                else:
+                    to_inner.append(r)
+            else:
+                r.inner += self.iters
+                rr, bb = sc[1][0], sc[1][5]
+                if math.sqrt(max(rr, 0.0)) <= self.inner_rtol * math.sqrt(max(bb, 1e-300)) \
+                        or r.inner >= self.max_inner or not math.isfinite(rr):
+                    to_outer.append(r)
+        with torch.cuda.stream(s):
+            for grp in self._chunks(to_inner):
+                nap.napspmv_cg_batch_init([r.inner_slot for r in grp], nap.PREC_F32,
+                                          x_is_zero=True, stream=s)
+            for grp in self._chunks(to_outer):
+                nap.napspmv_batch_add([r.x for r in grp], [r.d for r in grp], stream=s)
+        for r in to_inner:
+            r.state = "inner"
+        for r in to_outer:
+            r.state = "outer"
+            r.outer += 1
+        self.steps += 1
+
+    # ------------------------------------------------------------ driver
+    def run(self, specs, realtime=True):
+        """Serve `specs` (dicts from inputs.serving_requests).  With realtime,
+        request q becomes visible at t0 + arrival; otherwise all are queued at
+        once.  Returns the list of finished Request objects."""
+        reqs = [Request(s) for s in specs]
+        pending = collections.deque(sorted(reqs, key=lambda r: r.arrival))
+        queue: collections.deque = collections.deque()
+        active = []
+        t0 = time.perf_counter()
+        for r in reqs:
+            r.t_arrive = t0 + (r.arrival if realtime else 0.0)
+        while pending or queue or active:
+            now = time.perf_counter()
+            while pending and pending[0].t_arrive <= now:
+                queue.append(pending.popleft())
+            while queue and len(active) < self.max_active:
+                if not self._admit(queue[0]):
+                    break
+                active.append(queue.popleft())
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(0.01, pending[0].t_arrive - time.perf_counter())))
+                    continue
+                if queue:
+                    raise RuntimeError("request does not fit the memory budget")
+            self._step(active)
+            active = [r for r in active if r.state != "done"]
+        return reqs
+
+
+def summarize(reqs, wall_s):
+    lat = np.array([r.t_done - r.t_arrive for r in reqs])
+    return {"requests": len(reqs), "throughput_rps": len(reqs) / wall_s,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3)}
