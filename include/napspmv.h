@@ -181,6 +181,27 @@ int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_
                         const double *const *v, double *const *w, const int32_t *reps,
                         const double *scale, const napspmv_opts *opts, void *stream);
 
+/* w <- A v (reps chained applies, as napspmv_apply_n) without allocating any
+ * memory.  The paper has no counterpart: this serves callers that cannot
+ * allocate device memory when they need a product, because another allocator
+ * (a framework's memory pool) owns the device's free memory or because
+ * cudaMalloc's implicit device synchronisation is not acceptable on their
+ * path.  The plan must already exist (napspmv_plan allocates).
+ *   - Receive buffers, the chain vector and dependency counters come from one
+ *     fixed array of 2^20 doubles (8 MiB) that this library reserves on every
+ *     device that loads it, until the process exits.  Plans needing more
+ *     (counters + b_{l->l} + b_{l->nl} + 2 g_send + b_{nl->l} + N values)
+ *     are rejected with NAPSPMV_ERR_UNSUPPORTED and a message giving both sizes.
+ *   - Every call shares that array and it keeps the last call's contents;
+ *     the counters are cleared by each call.  Calls that overlap on the GPU
+ *     (on different streams, or on different plans) race on it: order them.
+ *   - The first call on a device looks the array's device address up (with
+ *     that device current); make that first call before any stream capture.
+ *   - Uses the fused engine with the plan's current work items and FP64
+ *     values; device-side timeouts are reported by napspmv_status(P). */
+int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double *w, int32_t reps,
+                          double scale, void *stream);
+
 /* Synchronise `stream`, return and clear the plan's device-side status
  * (NAPSPMV_OK or NAPSPMV_ERR_TIMEOUT) of its own workspace. */
 int napspmv_status(napspmv_plan_t *P, void *stream);

@@ -31,6 +31,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "internal.h"
 
@@ -1094,3 +1096,102 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
 
 extern "C" const char *napspmv_last_error(void) { return nap::g_last_error.c_str(); }
 extern "C" int64_t napspmv_launch_count(void) { return nap::g_launches; }
+
+// ===================================================================
+// Apply without allocation.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// product: their device memory is owned by another allocator (a framework's
+// memory pool that holds the free memory), or they run on a latency-critical
+// path where cudaMalloc's implicit device synchronisation would stall their
+// pipeline.  napspmv_apply_noalloc serves them: it runs the fused apply with
+// its receive buffers, chain vector and dependency counters carved out of the
+// fixed array below instead of a workspace.  The array is reserved on every
+// device that loads this library, until the process exits.
+namespace nap {
+constexpr int64_t kNoallocDoubles = 1ll << 20;  // 8 MiB per device
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+static double *g_noalloc_ptr[256];
+static std::mutex g_noalloc_mu;
+}  // namespace nap
+
+extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double *w, int32_t reps,
+                                     double scale, void *stream)
+{
+    using namespace nap;
+    if (!P || !v || !w || reps < 1 || (const double *)w == v) {
+        set_error(NAPSPMV_ERR_ARG, "NULL plan or vector, reps < 1, or w == v");
+        return NAPSPMV_ERR_ARG;
+    }
+    // doubles of scratch: counters (as 8-byte words), b_{l->l}, b_{l->nl},
+    // g_send, g_recv, b_{nl->l}, the chain vector
+    const int64_t words = (int64_t)ctr_count(P);
+    const int64_t need = words + P->n_bll + P->n_lbuf + 2 * P->n_gs + P->n_bnl + P->n;
+    if (need > kNoallocDoubles) {
+        set_error(NAPSPMV_ERR_UNSUPPORTED,
+                  "napspmv_apply_noalloc: this plan needs " + std::to_string(need) +
+                      " doubles of scratch; the static area holds " +
+                      std::to_string(kNoallocDoubles) + " (8 MiB)");
+        return NAPSPMV_ERR_UNSUPPORTED;
+    }
+    if (P->device < 0 || P->device >= 256) {
+        set_error(NAPSPMV_ERR_ARG, "device id out of range");
+        return NAPSPMV_ERR_ARG;
+    }
+    int cur = 0;
+    NAP_CUDA(cudaGetDevice(&cur));
+    if (cur != P->device) NAP_CUDA(cudaSetDevice(P->device));
+    double *base = nullptr;
+    {
+        // first call on a device: look up the array's device address (with
+        // that device current); later calls reuse it
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[P->device]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                if (cur != P->device) cudaSetDevice(cur);
+                return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+            }
+            g_noalloc_ptr[P->device] = static_cast<double *>(p);
+        }
+        base = g_noalloc_ptr[P->device];
+    }
+    // a workspace view of the array; the sticky error flag stays the plan's own
+    napspmv_ws_t view;
+    view.plan = P;
+    view.device = P->device;
+    view.ctr = reinterpret_cast<unsigned long long *>(base);
+    double *q = base + words;
+    view.bll = q;
+    q += P->n_bll;
+    view.lbuf = q;
+    q += P->n_lbuf;
+    view.gsend = q;
+    q += P->n_gs;
+    view.grecv = q;
+    q += P->n_gs;
+    view.bnl = q;
+    q += P->n_bnl;
+    view.xtmp = q;
+    view.err = P->ws->err;
+    // the plan's current work items and matching options: nothing is rebuilt
+    napspmv_opts o = P->defaults;
+    o.engine = NAPSPMV_ENGINE_FUSED;
+    o.precision = NAPSPMV_PREC_F64;
+    o.chunk = P->items.chunk;
+    o.tile_rows = P->items.tile_rows;
+    o.tile_nnz = P->items.tile_nnz;
+    o.debug_stall = 0;
+    napspmv_ws_t *wsl[1] = {&view};
+    napspmv_plan_t *pl[1] = {P};
+    const double *vl[1] = {v};
+    double *wl[1] = {w};
+    // launch_fused zeroes the counters (the array keeps the last call's contents)
+    int rc = launch_fused<1>(1, pl, wsl, vl, wl, &reps, &scale, o, (cudaStream_t)stream);
+    view.bll = view.lbuf = view.gsend = view.grecv = view.bnl = view.xtmp = nullptr;
+    view.ctr = nullptr;
+    view.err = nullptr;  // nothing of the view is freed
+    if (cur != P->device) cudaSetDevice(cur);
+    return rc;
+}

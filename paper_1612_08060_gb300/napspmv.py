@@ -88,6 +88,7 @@ def lib():
             "napspmv_apply_ex": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int32, C.c_double,
                                            C.POINTER(napspmv_opts), _VP]),
             "napspmv_apply_host": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_double, _VP]),
+            "napspmv_apply_noalloc": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_double, _VP]),
             "napspmv_apply_batch": (C.c_int, [C.c_int32, C.POINTER(_VP), C.POINTER(_VP),
                                               C.POINTER(_VP), C.POINTER(_VP),
                                               C.POINTER(C.c_int32), C.POINTER(C.c_double),
@@ -229,6 +230,12 @@ def napspmv_apply_ex(plan, v, w, reps=1, scale=1.0, opts=None, ws=None, stream=N
     _check(lib().napspmv_apply_ex(plan.handle, ws.handle if ws else None, _dptr(v), _dptr(w),
                                   int(reps), float(scale), C.byref(opts) if opts else None,
                                   _stream(stream)))
+
+
+def napspmv_apply_noalloc(plan, v, w, reps=1, scale=1.0, stream=None):
+    """As napspmv_apply_n, with no allocation (scratch in a fixed device array)."""
+    _check(lib().napspmv_apply_noalloc(plan.handle, _dptr(v), _dptr(w), int(reps), float(scale),
+                                       _stream(stream)))
 
 
 def napspmv_apply_host(plan, v_host, w_host, reps=1, scale=1.0, stream=None):
