@@ -42,6 +42,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, device=None):
+    """Max of a float over all ranks of the default process group (the identity
+    without one).  Works with nccl (CUDA tensor) and gloo (CPU tensor)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = device if (device is not None and dist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world_size, bytes_per_apply, reps, steps, max_ms):
+    """Whole-job GB/s: every replica's bytes over the slowest rank's time."""
+    return world_size * bytes_per_apply * reps * steps / (max_ms * 1e-3) / 1e9
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -278,11 +296,8 @@ def main():
         assert rc == 0, rc
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * B * args.reps * args.steps / (total_ms * 1e-3) / 1e9
+    total_ms = max_over_ranks(total_ms, dev)
+    value = job_value(ws, B, args.reps, args.steps, total_ms)
     avg_launch = statistics.mean(per)
     achieved = B * args.reps / (avg_launch * 1e-3) / 1e9
     peak, peak_kind = peaks()

@@ -83,12 +83,6 @@ __device__ __forceinline__ float ld_stream_f32(const float *p)
     asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ long long globaltimer()
 {
     long long t;
@@ -96,13 +90,15 @@ __device__ __forceinline__ long long globaltimer()
     return t;
 }
 
-// Vector loads: data written earlier in the same launch is read through L2
-// (L1 is not coherent across SMs); in the phased engine every vector is
+// Vector loads.  Fused engine: data written earlier in the same launch by
+// other CTAs is read with plain (weak, L1-cacheable) loads; they are ordered
+// after the producers' writes by thread 0's acquire fence on the dependency
+// counters followed by the CTA barrier.  Phased engine: every vector is
 // read-only for the kernel's lifetime and may use the read-only path.
 template <bool INKERNEL>
 __device__ __forceinline__ double ldx(const double *p)
 {
-    if (INKERNEL) return __ldcg(p);
+    if (INKERNEL) return *p;
     return __ldg(p);
 }
 
@@ -433,22 +429,55 @@ struct FusedParams {
     Job jobs[MAXJ];
 };
 
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Spin (bounded) until *p >= target; relaxed loads, the caller fences.
 __device__ __forceinline__ bool wait_ge(const unsigned long long *p, unsigned long long target,
                                         int *err, long long timeout_ns)
 {
-    if (target == 0 || ld_acquire(p) >= target) return true;
+    if (target == 0 || ld_relaxed(p) >= target) return true;
     const long long t0 = globaltimer();
     unsigned ns = 32;
     for (;;) {
         if (*(volatile int *)err) return false;
         __nanosleep(ns);
         if (ns < 1024) ns <<= 1;
-        if (ld_acquire(p) >= target) return true;
+        if (ld_relaxed(p) >= target) return true;
         if (globaltimer() - t0 > timeout_ns) {
             atomicCAS(err, 0, 1);
             return false;
         }
     }
+}
+
+struct Cond {
+    const unsigned long long *p;
+    unsigned long long t;
+};
+// All conditions: first one round of independent loads; only if one is not
+// yet met, spin on it.  Ends with the acquire fence that orders every later
+// load of this thread (and, through the CTA barrier, of the CTA) after the
+// producers' writes.
+__device__ __forceinline__ bool wait_all(const Cond *c, int n, int *err, long long tmo)
+{
+    unsigned long long v[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) v[i] = (i < n && c[i].t) ? ld_relaxed(c[i].p) : 0ull;
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        if (i < n && v[i] < c[i].t) ok = false;
+    if (!ok)
+        for (int i = 0; i < n; i++)
+            if (!wait_ge(c[i].p, c[i].t, err, tmo)) return false;
+    fence_acq_rel();
+    return true;
 }
 
 __device__ __noinline__ bool item_deps(const Job &J, const Item &it, int k, long long tmo, bool stall)
@@ -458,34 +487,42 @@ __device__ __noinline__ bool item_deps(const Job &J, const Item &it, int k, long
     const unsigned long long kk = k, k1 = k + 1;
     const int n = it.node;
     if (stall && !wait_ge(J.ctr + 1 + kNumCounters * J.nn, 1, J.err, tmo)) return false;
+    Cond c[4];
+    int m = 0;
     switch (it.kind) {
     case kGatherJ2:
     case kGatherJ0:
         // x_k rows of node n written; previous readers of b_{l->l}, b_{l->nl} done
-        return wait_ge(C(kC5, n), kk * N(kC5, n), J.err, tmo) &&
-               wait_ge(C(kC2, n), kk * N(kC2, n), J.err, tmo);
+        c[m++] = {C(kC5, n), kk * N(kC5, n)};
+        c[m++] = {C(kC2, n), kk * N(kC2, n)};
+        break;
     case kPack:
-        return wait_ge(C(kC1, n), k1 * N(kC1, n), J.err, tmo) &&
-               wait_ge(C(kC5, n), kk * N(kC5, n), J.err, tmo) &&
-               wait_ge(C(kC3, n), kk * N(kC3, n), J.err, tmo);
-    case kTransfer: {
-        if (!wait_ge(C(kC2, n), k1 * N(kC2, n), J.err, tmo)) return false;
-        if (k == 0) return true;
-        for (int m = it.msg; J.msg_off[m] < it.e; m++) {
-            const int dn = J.msg_dstnode[m];
-            if (!wait_ge(C(kC4, dn), kk * N(kC4, dn), J.err, tmo)) return false;
+        c[m++] = {C(kC1, n), k1 * N(kC1, n)};
+        c[m++] = {C(kC5, n), kk * N(kC5, n)};
+        c[m++] = {C(kC3, n), kk * N(kC3, n)};
+        break;
+    case kTransfer:
+        c[m++] = {C(kC2, n), k1 * N(kC2, n)};
+        if (k > 0) {
+            // previous readers of the destination nodes' g_recv slots done
+            for (int q = it.msg; J.msg_off[q] < it.e; q++) {
+                const int dn = J.msg_dstnode[q];
+                if (!wait_ge(C(kC4, dn), kk * N(kC4, dn), J.err, tmo)) return false;
+            }
         }
-        return true;
-    }
+        break;
     case kUnpack:
-        return wait_ge(C(kArr, n), k1 * N(kArr, n), J.err, tmo) &&
-               wait_ge(C(kC5, n), kk * N(kC5, n), J.err, tmo);
+        c[m++] = {C(kArr, n), k1 * N(kArr, n)};
+        c[m++] = {C(kC5, n), kk * N(kC5, n)};
+        break;
     default:  // kSpmv
-        return wait_ge(C(kC1, n), k1 * N(kC1, n), J.err, tmo) &&
-               wait_ge(C(kC4, n), k1 * N(kC4, n), J.err, tmo) &&
-               wait_ge(C(kC5, n), kk * N(kC5, n), J.err, tmo) &&
-               wait_ge(C(kC2, n), kk * N(kC2, n), J.err, tmo);
+        c[m++] = {C(kC1, n), k1 * N(kC1, n)};
+        c[m++] = {C(kC4, n), k1 * N(kC4, n)};
+        c[m++] = {C(kC5, n), kk * N(kC5, n)};
+        c[m++] = {C(kC2, n), kk * N(kC2, n)};
+        break;
     }
+    return wait_all(c, m, J.err, tmo);
 }
 
 __device__ __noinline__ void item_signal(const Job &J, const Item &it)
@@ -508,31 +545,31 @@ __device__ __noinline__ void item_signal(const Job &J, const Item &it)
 }
 
 // The element work of the message steps (shared by both engines).
-template <bool INKERNEL>
+template <bool INKERNEL, int U>
 __device__ __noinline__ void step_gather(double *dst, const double *src, const int32_t *idx,
                                             int b, int e, int tid)
 {
-    batched<4>(
+    batched<U>(
         b, e, tid, [&](int k) { return (uint32_t)ld_stream_s32(idx + k); },
         [&](int, uint32_t j) { return ldx<INKERNEL>(src + j); },
         [&](int k, uint32_t, double v) { dst[k] = v; });
 }
-template <bool INKERNEL>
+template <bool INKERNEL, int U>
 __device__ __noinline__ void step_pack(double *gsend, const double *x, const double *lbuf,
                                           const uint32_t *src, int b, int e, int tid)
 {
-    batched<4>(
+    batched<U>(
         b, e, tid, [&](int k) { return ld_stream_u32(src + k); },
         [&](int, uint32_t u) {
             return (u & kFromLbuf) ? ldx<INKERNEL>(lbuf + (u & ~kFromLbuf)) : ldx<INKERNEL>(x + u);
         },
         [&](int k, uint32_t, double v) { gsend[k] = v; });
 }
-template <bool INKERNEL>
+template <bool INKERNEL, int U>
 __device__ __noinline__ void step_transfer(double *grecv, const double *gsend,
                                               const int32_t *dst, int b, int e, int tid)
 {
-    batched<4>(
+    batched<U>(
         b, e, tid, [&](int k) { return (uint32_t)ld_stream_s32(dst + k); },
         [&](int k, uint32_t) { return ldx<INKERNEL>(gsend + k); },
         [&](int, uint32_t d, double v) { grecv[d] = v; });
@@ -615,11 +652,11 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
         const double *x = (k == 0) ? J.v : (((J.reps - k) & 1) == 0 ? J.w : J.xtmp);
         double *y = (((J.reps - 1 - k) & 1) == 0) ? J.w : J.xtmp;
         switch (it.kind) {
-        case kGatherJ2: step_gather<true>(J.bll, x, J.bll_j, it.b, it.e, tid); break;
-        case kGatherJ0: step_gather<true>(J.lbuf, x, J.lbuf_j, it.b, it.e, tid); break;
-        case kPack: step_pack<true>(J.gsend, x, J.lbuf, J.pack_src, it.b, it.e, tid); break;
-        case kTransfer: step_transfer<true>(J.grecv, J.gsend, J.xfer_dst, it.b, it.e, tid); break;
-        case kUnpack: step_gather<true>(J.bnl, J.grecv, J.unp_src, it.b, it.e, tid); break;
+        case kGatherJ2: step_gather<true, 4>(J.bll, x, J.bll_j, it.b, it.e, tid); break;
+        case kGatherJ0: step_gather<true, 4>(J.lbuf, x, J.lbuf_j, it.b, it.e, tid); break;
+        case kPack: step_pack<true, 4>(J.gsend, x, J.lbuf, J.pack_src, it.b, it.e, tid); break;
+        case kTransfer: step_transfer<true, 4>(J.grecv, J.gsend, J.xfer_dst, it.b, it.e, tid); break;
+        case kUnpack: step_gather<true, 4>(J.bnl, J.grecv, J.unp_src, it.b, it.e, tid); break;
         default:
             if (staged_tile(it, cap)) {
                 const TileStage st = tile_stage(smem, cur, cap, trows);
@@ -634,7 +671,7 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
         seq++;
         __syncthreads();
         if (tid == 0) {
-            __threadfence();
+            fence_acq_rel();  // the CTA's writes (ordered by the barrier) before the counters
             item_signal(J, it);
             s_t = next;
         }
@@ -650,10 +687,10 @@ __global__ void __launch_bounds__(NT)
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n_bll + n_lbuf; b += gridDim.x * per) {
         const int e = min(b + per, n_bll + n_lbuf);
-        if (b < n_bll) step_gather<false>(bll, x, bll_j, b, min(e, n_bll), threadIdx.x);
+        if (b < n_bll) step_gather<false, 8>(bll, x, bll_j, b, min(e, n_bll), threadIdx.x);
         if (e > n_bll) {
             const int lb = max(b, n_bll) - n_bll, le = e - n_bll;
-            step_gather<false>(lbuf, x, lbuf_j, lb, le, threadIdx.x);
+            step_gather<false, 8>(lbuf, x, lbuf_j, lb, le, threadIdx.x);
         }
     }
 }
@@ -662,21 +699,21 @@ __global__ void __launch_bounds__(NT)
 {
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
-        step_pack<false>(gsend, x, lbuf, src, b, min(b + per, n), threadIdx.x);
+        step_pack<false, 8>(gsend, x, lbuf, src, b, min(b + per, n), threadIdx.x);
 }
 __global__ void __launch_bounds__(NT)
     k_transfer(const double *gsend, const int32_t *dst, double *grecv, int n)
 {
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
-        step_transfer<false>(grecv, gsend, dst, b, min(b + per, n), threadIdx.x);
+        step_transfer<false, 8>(grecv, gsend, dst, b, min(b + per, n), threadIdx.x);
 }
 __global__ void __launch_bounds__(NT)
     k_unpack(const double *grecv, const int32_t *src, double *bnl, int n)
 {
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
-        step_gather<false>(bnl, grecv, src, b, min(b + per, n), threadIdx.x);
+        step_gather<false, 8>(bnl, grecv, src, b, min(b + per, n), threadIdx.x);
 }
 template <int V, bool F32>
 __global__ void __launch_bounds__(NT)
@@ -825,6 +862,8 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
     NAP_CUDA(cudaMemcpy(d_cnt, cnt.data(), sizeof(uint64_t) * cnt.size(), cudaMemcpyHostToDevice));
     if (S.d_items) cudaFree(S.d_items);
     if (S.d_cnt) cudaFree(S.d_cnt);
+    for (auto &g : P->graphs) cudaGraphExecDestroy(g.exec);  // they captured the old items
+    P->graphs.clear();
     S.d_items = d_items;
     S.d_cnt = d_cnt;
     S.n_items = (int32_t)items.size();
@@ -953,8 +992,8 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
     return NAPSPMV_OK;
 }
 
-static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
-                         double scale, const napspmv_opts &o, cudaStream_t s)
+static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
+                          double scale, const napspmv_opts &o, cudaStream_t s, int64_t *kernels)
 {
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
     auto grid = [&](int64_t n) {
@@ -977,9 +1016,9 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
     }
 #undef NAP_CASE
     const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows);
-    if (int rc = prepare_smem(sp, sm)) return rc;
     const ItemSet &S = P->items;
     const int n_tiles = S.n_items - S.spmv_first;
+    int64_t nk = 0;
     for (int k = 0; k < reps; k++) {
         const double *x = (k == 0) ? v : (((reps - k) & 1) == 0 ? w : ws->xtmp);
         double *y = (((reps - 1 - k) & 1) == 0) ? w : ws->xtmp;
@@ -987,24 +1026,90 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
             k_gather2<<<grid(P->n_bll + P->n_lbuf), NT, 0, s>>>(
                 x, P->lists[L_BLL].d_idx, ws->bll, (int)P->n_bll, P->lists[L_LBUF].d_idx, ws->lbuf,
                 (int)P->n_lbuf);
-            count_launch(1);
+            nk++;
         }
         if (P->n_gs > 0) {
             k_pack<<<grid(P->n_gs), NT, 0, s>>>(x, ws->lbuf, P->d_pack_src, ws->gsend, (int)P->n_gs);
             k_transfer<<<grid(P->n_gs), NT, 0, s>>>(ws->gsend, P->d_xfer_dst, ws->grecv,
                                                     (int)P->n_gs);
-            count_launch(2);
+            nk += 2;
         }
         if (P->n_bnl > 0) {
             k_unpack<<<grid(P->n_bnl), NT, 0, s>>>(ws->grecv, P->d_unp_src, ws->bnl, (int)P->n_bnl);
-            count_launch(1);
+            nk++;
         }
         sp<<<std::max(1, std::min(n_tiles, P->num_sms * 4)), NT, sm, s>>>(
             A, x, ws->bll, ws->bnl, y, make_scale(scale), S.d_items + S.spmv_first, n_tiles,
             o.tile_nnz, o.tile_rows, ws->err);
-        count_launch(1);
+        nk++;
         NAP_CUDA(cudaGetLastError());
     }
+    *kernels = nk;
+    return NAPSPMV_OK;
+}
+
+// Chained applies on a capturable stream are recorded once into a CUDA graph
+// per (vectors, workspace, reps, scale, options) and replayed afterwards.
+static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
+                         double scale, const napspmv_opts &o, cudaStream_t s)
+{
+    {
+        const bool f32 = o.precision == NAPSPMV_PREC_F32;
+        const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows);
+        int rc = NAPSPMV_OK;
+#define NAP_CASE(V)                                                                  \
+    case V: rc = f32 ? prepare_smem(k_spmv<V, true>, sm) : prepare_smem(k_spmv<V, false>, sm); \
+        break;
+        switch (o.vec) {
+            NAP_CASE(1)
+            NAP_CASE(2)
+            NAP_CASE(4)
+            NAP_CASE(8)
+            NAP_CASE(16)
+            NAP_CASE(32)
+        }
+#undef NAP_CASE
+        if (rc) return rc;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NAP_CUDA(cudaStreamIsCapturing(s, &cs));
+    const bool use_graph = reps > 1 && s != nullptr && cs == cudaStreamCaptureStatusNone;
+    int64_t nk = 0;
+    if (!use_graph) {
+        int rc = enqueue_phased(P, ws, v, w, reps, scale, o, s, &nk);
+        if (!rc) count_launch(nk);
+        return rc;
+    }
+    for (size_t i = 0; i < P->graphs.size(); i++) {
+        auto &g = P->graphs[i];
+        if (g.v == v && g.w == w && g.ws == ws && g.reps == reps && g.scale == scale &&
+            g.prec == o.precision && g.vec == o.vec && g.tile_rows == o.tile_rows &&
+            g.tile_nnz == o.tile_nnz) {
+            NAP_CUDA(cudaGraphLaunch(g.exec, s));
+            count_launch(g.kernels);
+            return NAPSPMV_OK;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    NAP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_phased(P, ws, v, w, reps, scale, o, s, &nk);
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+    if (P->graphs.size() >= 8) {
+        cudaGraphExecDestroy(P->graphs.front().exec);
+        P->graphs.erase(P->graphs.begin());
+    }
+    P->graphs.push_back({v, w, ws, reps, o.precision, o.vec, o.tile_rows, o.tile_nnz, scale, exec, nk});
+    NAP_CUDA(cudaGraphLaunch(exec, s));
+    count_launch(nk);
     return NAPSPMV_OK;
 }
 

@@ -129,6 +129,15 @@ int napspmv_ws_create(napspmv_plan_t *P, napspmv_ws_t **out)
 void napspmv_ws_destroy(napspmv_ws_t *ws)
 {
     if (!ws || ws->owned_by_plan) return;
+    auto &G = ws->plan->graphs;  // graphs that captured this workspace's buffers
+    for (size_t i = 0; i < G.size();) {
+        if (G[i].ws == ws) {
+            cudaGraphExecDestroy(G[i].exec);
+            G.erase(G.begin() + i);
+        } else {
+            i++;
+        }
+    }
     ws_free(ws);
     delete ws;
 }

@@ -123,6 +123,15 @@ struct napspmv_plan_s {
     int32_t *d_gs_msg_dstnode = nullptr;
 
     nap::ItemSet items;
+    // instantiated CUDA graphs of chained phased applies, newest last
+    struct GraphEntry {
+        const void *v, *w, *ws;
+        int32_t reps, prec, vec, tile_rows, tile_nnz;
+        double scale;
+        cudaGraphExec_t exec;
+        int64_t kernels;
+    };
+    std::vector<GraphEntry> graphs;
     napspmv_opts defaults{};
     napspmv_stats stats{};
     napspmv_ws_t *ws = nullptr;  // the plan's own workspace

@@ -873,6 +873,7 @@ void plan_free(napspmv_plan_t *P)
         ws_free(P->ws);
         delete P->ws;
     }
+    for (auto &g : P->graphs) cudaGraphExecDestroy(g.exec);
     for (auto &L : P->lists)
         if (L.d_idx) cudaFree(L.d_idx);
     void *ptrs[] = {P->d_split, P->d_rowptr, P->d_colenc, P->d_val, P->d_val32, P->d_pack_src,

@@ -41,7 +41,7 @@ def test_alone_equals_mix_and_correct():
 def test_memory_budget_admission():
     from paper_1612_08060_gb300 import serve
     specs = _specs(count=12, seed=9, n_hi=5e4)
-    srv = serve.Server(mem_budget=24 << 20, max_active=64, keep_results=True)
+    srv = serve.Server(mem_budget=12 << 20, max_active=64, keep_results=True)
     reqs = srv.run(specs, realtime=False)
     assert all(r.state == "done" for r in reqs)
     assert max(srv.batch_sizes) < len(specs)  # the budget held some requests back
