@@ -218,15 +218,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--reps", type=int, default=100, help="chained applies per step")
-    ap.add_argument("--engine", default="fused", choices=["fused", "phased"])
+    ap.add_argument("--engine", default="default", choices=["default", "fused", "phased", "overlap"])
     ap.add_argument("--vec", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--tile-nnz", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="also compare continuous batching with the plain loop on this many "
+                         "requests of the serving mix")
+    ap.add_argument("--serve-nmax", type=float, default=2e5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -252,10 +257,16 @@ def main():
     st = nap.napspmv_plan_stats(plan)
     B = bytes_per_apply(A, st)
     B_csr = st["bytes_csr_f64"]
+    # SpMV step alone: row pointer, column + value streams, each x and each
+    # received value read once, w written once
+    B_spmv = 4.0 * (A.n + 1) + 12.0 * A.nnz + 16.0 * A.n + 8.0 * (st["bll_total"] +
+                                                                  st["bnl_total"])
     assert abs(B - (st["bytes_csr_f64"] + st["bytes_msg"])) < 1.0
-    opts = nap.make_opts(engine=nap.ENGINE_FUSED if args.engine == "fused" else nap.ENGINE_PHASED,
+    opts = nap.make_opts(engine={"default": nap.ENGINE_DEFAULT, "fused": nap.ENGINE_FUSED,
+                                 "phased": nap.ENGINE_PHASED,
+                                 "overlap": nap.ENGINE_OVERLAP}[args.engine],
                          vec=args.vec, chunk=args.chunk, tile_rows=args.tile_rows,
-                         tile_nnz=args.tile_nnz,
+                         tile_nnz=args.tile_nnz, stages=args.stages,
                          ctas_per_sm=args.ctas_per_sm)
     eff = nap.napspmv_get_default_opts(plan)
     stream = torch.cuda.Stream(device=dev)
@@ -294,6 +305,22 @@ def main():
         clocks = sampler.stop() if not args.no_clocks else None
         rc = nap.napspmv_status(plan, stream)
         assert rc == 0, rc
+    # the dominant kernel (three-block SpMV, a11) timed alone on the same stream
+    with torch.cuda.stream(stream):
+        nap.napspmv_apply_ex(plan, vd, wd, 1, 1.0, opts, stream=stream)
+        sp_n = 50
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        xd = torch.empty_like(vd)
+        for _ in range(3):
+            nap.napspmv_spmv_step(plan, vd, xd, 1.0, opts, stream=stream)
+        e0.record(stream)
+        for _ in range(sp_n):
+            nap.napspmv_spmv_step(plan, vd, xd, 1.0, opts, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        spmv_ms = e0.elapsed_time(e1) / sp_n
+        assert torch.equal(xd, wd), "SpMV step does not reproduce the apply"
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms = max_over_ranks(total_ms, dev)
@@ -325,20 +352,27 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": w.name, "n": A.n, "nnz": A.nnz, "n_p": w.n_p, "ppn": w.ppn,
-                   "applies_per_step": args.reps, "scale": SCALE, "engine": args.engine,
+                   "applies_per_step": args.reps, "scale": SCALE,
+                   "engine": {1: "fused", 2: "phased", 3: "overlap"}[opts.engine or eff.engine],
                    "vec": opts.vec or eff.vec, "chunk": opts.chunk or eff.chunk,
                    "tile_rows": opts.tile_rows or eff.tile_rows,
                    "tile_nnz": opts.tile_nnz or eff.tile_nnz,
+                   "stages": opts.stages or eff.stages,
                    "l2": "inputs larger than L2: each apply streams the 175 MB col/val "
                          "arrays (L2 129 MB); not flushed between steps",
                    "parallelism": f"replicas{ws}"},
         "bytes_per_apply": {"total": B, "csr": B_csr, "msg": st["bytes_msg"]},
         "csr_gbs": round(B_csr * args.reps / (avg_launch * 1e-3) / 1e9, 3),
         "gflops": round(2.0 * A.nnz * args.reps / (avg_launch * 1e-3) / 1e9, 3),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+        "roofline": {"bound": "hbm", "achieved": round(B_spmv / (spmv_ms * 1e-3) / 1e9, 3),
+                     "peak": peak, "unit": "GB/s",
+                     "frac": round(B_spmv / (spmv_ms * 1e-3) / 1e9 / peak, 4),
                      "peak_kind": peak_kind, "traffic": ncu_traffic(),
-                     "kernel": "k_fused (one launch = 100 chained applies)"},
+                     "kernel": "k_spmv (three-block SpMV step, one launch = one apply's rows)",
+                     "algorithmic_bytes": B_spmv, "launch_ms": round(spmv_ms, 5)},
+        "step_roofline": {"bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
+                          "frac": round(achieved / peak, 4),
+                          "what": "whole apply (message steps + SpMV), algorithmic bytes"},
         "gpu_launches": int(launches),
         "plan": {"gpu_plan_ms": round(plan_ms, 2), "std_msgs": st["std_msgs"],
                  "std_inter_msgs": st["std_inter_msgs"], "std_inter_vals": st["std_inter_vals"],
@@ -349,6 +383,9 @@ def main():
     }
     if not args.no_cpu and ws == 1:
         line["cpu_baseline"] = cpu_baseline_leg(A, v, w_one, B, args.cpu_budget)
+    if args.serve > 0 and ws == 1:
+        from paper_1612_08060_gb300 import serve
+        line["serving"] = serve.compare(args.serve, n_hi=args.serve_nmax, device=dev)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -71,8 +71,17 @@ extern "C" {
 #define NAPSPMV_PREC_F64 0 /* FP64 values, FP64 products and sums            */
 #define NAPSPMV_PREC_F32 1 /* FP32-stored values, FP32 products, FP64 sums   */
 
-#define NAPSPMV_ENGINE_FUSED 0  /* one persistent launch for all phases     */
-#define NAPSPMV_ENGINE_PHASED 1 /* one kernel per phase (control variant)   */
+#define NAPSPMV_ENGINE_DEFAULT 0 /* the plan's default engine               */
+#define NAPSPMV_ENGINE_FUSED 1   /* one persistent launch for all phases and
+                                    all chained applies (dataflow items)     */
+#define NAPSPMV_ENGINE_PHASED 2  /* one kernel per phase; chains of applies
+                                    are captured once into a CUDA graph      */
+#define NAPSPMV_ENGINE_OVERLAP 3 /* as PHASED, with the on_process part of
+                                    the SpMV on a second stream while the
+                                    message steps run (Algorithm NAPSpMV's
+                                    overlap); the remote part then continues
+                                    each row's sum (with vec = 1 the same
+                                    bits as PHASED and FUSED)                */
 
 typedef struct napspmv_plan_s napspmv_plan_t;
 typedef struct napspmv_ws_s napspmv_ws_t;
@@ -95,18 +104,23 @@ typedef struct {
  * napspmv_set_default_opts, e.g. from an autotuner, may change). */
 typedef struct {
     int32_t precision;   /* NAPSPMV_PREC_F64 or NAPSPMV_PREC_F32               */
-    int32_t engine;      /* NAPSPMV_ENGINE_FUSED or NAPSPMV_ENGINE_PHASED      */
+    int32_t engine;      /* NAPSPMV_ENGINE_DEFAULT, _FUSED, _PHASED, _OVERLAP  */
     int32_t vec;         /* lanes per matrix row: 1, 2, 4, 8, 16 or 32         */
     int32_t ctas_per_sm; /* persistent CTAs per SM (fused engine)              */
     int32_t chunk;       /* gather elements per work item (fused engine)       */
     int32_t tile_rows;   /* at most this many matrix rows per SpMV work item   */
     int32_t tile_nnz;    /* at most this many stored entries per SpMV work item
-                            (their products are staged in shared memory); a
-                            longer single row gets a tile of its own           */
+                            (staged in shared memory by bulk copies); a longer
+                            single row gets a tile of its own                  */
+    int32_t stages;      /* shared-memory stages of the phased SpMV pipeline
+                            (2..4; the fused engine always uses 2)             */
     int32_t timeout_ms;  /* limit of every device-side wait                    */
-    int32_t debug_stall; /* test hook: 1 makes the first work item wait on a
-                            counter nothing increments, so the launch ends
-                            with NAPSPMV_ERR_TIMEOUT after timeout_ms          */
+    int32_t debug_stall; /* test hook (fused engine): 1 makes the first work
+                            item wait on a counter nothing increments, so the
+                            launch ends with NAPSPMV_ERR_TIMEOUT after
+                            timeout_ms.  After any device-side error every
+                            kernel of the workspace skips its work until
+                            napspmv_status clears the flag.                    */
 } napspmv_opts;
 
 /* Communication statistics of a plan.  Counts are numbers of messages and
@@ -166,6 +180,14 @@ int napspmv_apply_n(napspmv_plan_t *P, const double *v, double *w, int32_t reps,
  * dependency counters of one in-flight apply. */
 int napspmv_apply_ex(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w,
                      int32_t reps, double scale, const napspmv_opts *opts, void *stream);
+
+/* The three-block SpMV step alone (the three local_spmv calls of Algorithm
+ * NAPSpMV, Sec. 4): w <- scale (A_on_process v + A_on_node b_{l->l} +
+ * A_off_node b_{nl->l}) with the receive buffers the workspace (NULL = the
+ * plan's own) holds from its last apply.  For measuring the step on its own;
+ * after an apply of v it reproduces that apply's w.  Asynchronous. */
+int napspmv_spmv_step(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w,
+                      double scale, const napspmv_opts *opts, void *stream);
 
 /* End-to-end variant on HOST vectors (pageable or pinned): copies v in,
  * runs reps chained applies, copies w out and synchronises `stream`.

@@ -208,8 +208,8 @@ __host__ __device__ __forceinline__ StageLayout stage_layout(int cap, int tile_r
     L.bytes = L.val + align16(8 * (cap + 8));
     return L;
 }
-constexpr int kStages = 2;
-constexpr int kMbarBytes = 16 * kStages;  // one 8-byte mbarrier per stage, 16-byte slots
+constexpr int kMaxStages = 4;
+constexpr int kMbarBytes = 16 * kMaxStages;  // one 8-byte mbarrier per stage, 16-byte slots
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -315,8 +315,13 @@ __device__ __forceinline__ bool tile_wait(const TileStage &st, uint32_t parity, 
     }
 }
 
+// What a row sum covers: the whole three-block row (FULL), only its
+// on_process part (LOCAL: the partial, unscaled, goes to y), or its remote
+// part (REMOTE: the FMA chain continues from the partial in y, then scales).
+enum SpmvMode { kFull = 0, kLocal = 1, kRemote = 2 };
+
 // Rows [r0, r1) from a staged tile.
-template <int V, bool F32, bool INKERNEL>
+template <int V, bool F32, bool INKERNEL, int MODE = kFull>
 __device__ __forceinline__ void tile_compute(const TileStage &st, const double *x, const double *bll,
                                              const double *bnl, double *y, const Scale sc, int r0,
                                              int r1, int k0, int tid)
@@ -328,9 +333,10 @@ __device__ __forceinline__ void tile_compute(const TileStage &st, const double *
     for (int base = 0; base < nr; base += groups) {
         const int i = base + grp;
         double acc = 0.0;
+        if (MODE == kRemote && i < nr && lane == 0) acc = y[r0 + i];
         if (i < nr) {
             const int s = st.rows[r0 - rb + i] - kb, e = st.rows[r0 - rb + i + 1] - kb;
-#pragma unroll 4
+#pragma unroll 8
             for (int k = s + lane; k < e; k += V) {
                 const double xv = load_x<INKERNEL>(st.col[k], x, bll, bnl);
                 if (F32)
@@ -344,13 +350,13 @@ __device__ __forceinline__ void tile_compute(const TileStage &st, const double *
             for (int o = V / 2; o > 0; o >>= 1)
                 acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
         }
-        if (i < nr && lane == 0) y[r0 + i] = apply_scale(acc, sc);
+        if (i < nr && lane == 0) y[r0 + i] = MODE == kLocal ? acc : apply_scale(acc, sc);
     }
 }
 
 // A single row with more stored entries than a stage holds: read straight from
 // global memory, the whole CTA on the row (fixed strides, fixed-order tree).
-template <bool F32, bool INKERNEL>
+template <bool F32, bool INKERNEL, int MODE = kFull>
 __device__ void row_direct(const Csr3 &A, const double *x, const double *bll, const double *bnl,
                            double *y, const Scale sc, int r0, int r1, double *red, int tid)
 {
@@ -370,28 +376,28 @@ __device__ void row_direct(const Csr3 &A, const double *x, const double *bll, co
         if ((tid & 31) == 0) red[tid >> 5] = acc;
         __syncthreads();
         if (tid == 0) {
-            double t = 0.0;
+            double t = MODE == kRemote ? y[i] : 0.0;
             for (int q = 0; q < NT / 32; q++) t = __dadd_rn(t, red[q]);
-            y[i] = apply_scale(t, sc);
+            y[i] = MODE == kLocal ? t : apply_scale(t, sc);
         }
         __syncthreads();
     }
 }
 
-// Shared memory of the apply kernels: the two mbarriers, two stages, and a
-// small reduction area for row_direct.
-__host__ __device__ __forceinline__ int tile_smem_bytes(int cap, int tile_rows)
+// Shared memory of the apply kernels: the mbarriers, `ns` stages, and a small
+// reduction area for row_direct.
+__host__ __device__ __forceinline__ int tile_smem_bytes(int cap, int tile_rows, int ns)
 {
-    return kMbarBytes + kStages * stage_layout(cap, tile_rows).bytes + 8 * (NT / 32);
+    return kMbarBytes + ns * stage_layout(cap, tile_rows).bytes + 8 * (NT / 32);
 }
-__device__ __forceinline__ double *tile_red(unsigned char *base, int cap, int tile_rows)
+__device__ __forceinline__ double *tile_red(unsigned char *base, int cap, int tile_rows, int ns)
 {
-    return reinterpret_cast<double *>(base + kMbarBytes + kStages * stage_layout(cap, tile_rows).bytes);
+    return reinterpret_cast<double *>(base + kMbarBytes + ns * stage_layout(cap, tile_rows).bytes);
 }
-__device__ __forceinline__ void tile_smem_init(unsigned char *base)
+__device__ __forceinline__ void tile_smem_init(unsigned char *base, int ns)
 {
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; s++) mbar_init(reinterpret_cast<uint64_t *>(base + 16 * s), 1);
+        for (int s = 0; s < ns; s++) mbar_init(reinterpret_cast<uint64_t *>(base + 16 * s), 1);
         fence_barrier_init();
     }
     __syncthreads();
@@ -597,8 +603,8 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
     __shared__ int s_ok;
     const int tid = threadIdx.x;
     const int cap = prm.cap, trows = prm.tile_rows;
-    tile_smem_init(smem);
-    double *red = tile_red(smem, cap, trows);
+    tile_smem_init(smem, 2);
+    double *red = tile_red(smem, cap, trows, 2);
     uint32_t phase = 0;  // per-stage mbarrier parity, identical in every thread
     int seq = 0;         // items taken by this CTA; item seq uses stage seq & 1
     long long next = 0;
@@ -682,8 +688,9 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
 // --------------------------------------------------------- phased engine
 __global__ void __launch_bounds__(NT)
     k_gather2(const double *x, const int32_t *bll_j, double *bll, int n_bll, const int32_t *lbuf_j,
-              double *lbuf, int n_lbuf)
+              double *lbuf, int n_lbuf, const int *err)
 {
+    if (*(volatile const int *)err) return;  // sticky error: no work until cleared
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n_bll + n_lbuf; b += gridDim.x * per) {
         const int e = min(b + per, n_bll + n_lbuf);
@@ -695,57 +702,71 @@ __global__ void __launch_bounds__(NT)
     }
 }
 __global__ void __launch_bounds__(NT)
-    k_pack(const double *x, const double *lbuf, const uint32_t *src, double *gsend, int n)
+    k_pack(const double *x, const double *lbuf, const uint32_t *src, double *gsend, int n,
+           const int *err)
 {
+    if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
         step_pack<false, 8>(gsend, x, lbuf, src, b, min(b + per, n), threadIdx.x);
 }
 __global__ void __launch_bounds__(NT)
-    k_transfer(const double *gsend, const int32_t *dst, double *grecv, int n)
+    k_transfer(const double *gsend, const int32_t *dst, double *grecv, int n, const int *err)
 {
+    if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
         step_transfer<false, 8>(grecv, gsend, dst, b, min(b + per, n), threadIdx.x);
 }
 __global__ void __launch_bounds__(NT)
-    k_unpack(const double *grecv, const int32_t *src, double *bnl, int n)
+    k_unpack(const double *grecv, const int32_t *src, double *bnl, int n, const int *err)
 {
+    if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
         step_gather<false, 8>(bnl, grecv, src, b, min(b + per, n), threadIdx.x);
 }
-template <int V, bool F32>
+template <int V, bool F32, int MODE = kFull>
 __global__ void __launch_bounds__(NT)
     k_spmv(Csr3 A, const double *x, const double *bll, const double *bnl, double *y, Scale sc,
-           const Item *tiles, int n_tiles, int cap, int trows, int *err)
+           const Item *tiles, int n_tiles, int cap, int trows, int ns, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
-    tile_smem_init(smem);
-    double *red = tile_red(smem, cap, trows);
+    if (*(volatile const int *)err) return;  // sticky error: no work until cleared
+    tile_smem_init(smem, ns);
+    double *red = tile_red(smem, cap, trows, ns);
     uint32_t phase = 0;
-    int q = blockIdx.x;
-    if (tid == 0 && q < n_tiles) {
+    const int G = gridDim.x;
+    // tiles q = blockIdx.x + i G, i = 0, 1, ...; tile i uses stage i % ns and is
+    // requested ns - 1 tiles ahead
+    if (tid == 0)
+        for (int i = 0; i < ns - 1; i++) {
+            const int q = blockIdx.x + i * G;
+            if (q >= n_tiles) break;
+            const Item it = tiles[q];
+            if (staged_tile(it, cap))
+                tile_issue<F32>(A, tile_stage(smem, i, cap, trows), it.b, it.e, it.k0, it.k1);
+        }
+    int cur = 0;
+    for (int i = 0, q = blockIdx.x; q < n_tiles; i++, q += G) {
         const Item it = tiles[q];
-        if (staged_tile(it, cap)) tile_issue<F32>(A, tile_stage(smem, 0, cap, trows), it.b, it.e, it.k0, it.k1);
-    }
-    for (int i = 0; q < n_tiles; q += gridDim.x, i++) {
-        const Item it = tiles[q];
-        const int cur = i & 1, qn = q + gridDim.x;
-        if (tid == 0 && qn < n_tiles) {
-            const Item itn = tiles[qn];
-            if (staged_tile(itn, cap))
-                tile_issue<F32>(A, tile_stage(smem, cur ^ 1, cap, trows), itn.b, itn.e, itn.k0, itn.k1);
+        const int qa = q + (ns - 1) * G;
+        if (tid == 0 && qa < n_tiles) {
+            const Item ita = tiles[qa];
+            const int sa = (cur + ns - 1) % ns;  // the stage tile i - 1 used
+            if (staged_tile(ita, cap))
+                tile_issue<F32>(A, tile_stage(smem, sa, cap, trows), ita.b, ita.e, ita.k0, ita.k1);
         }
         if (staged_tile(it, cap)) {
             const TileStage st = tile_stage(smem, cur, cap, trows);
             const bool ok = tile_wait(st, (phase >> cur) & 1, err);
             phase ^= 1u << cur;
-            if (ok) tile_compute<V, F32, false>(st, x, bll, bnl, y, sc, it.b, it.e, it.k0, tid);
+            if (ok) tile_compute<V, F32, false, MODE>(st, x, bll, bnl, y, sc, it.b, it.e, it.k0, tid);
         } else {
-            row_direct<F32, false>(A, x, bll, bnl, y, sc, it.b, it.e, red, tid);
+            row_direct<F32, false, MODE>(A, x, bll, bnl, y, sc, it.b, it.e, red, tid);
         }
+        cur = cur + 1 == ns ? 0 : cur + 1;
         __syncthreads();
     }
 }
@@ -778,20 +799,21 @@ napspmv_opts resolve_opts(const napspmv_plan_t *P, const napspmv_opts *o)
     napspmv_opts r = P->defaults;
     if (!o) return r;
     r.precision = o->precision;  // 0 is FP64, a real choice
-    r.engine = o->engine;
+    if (o->engine) r.engine = o->engine;
     if (o->vec) r.vec = o->vec;
     if (o->ctas_per_sm) r.ctas_per_sm = o->ctas_per_sm;
     if (o->chunk) r.chunk = o->chunk;
     if (o->tile_rows) r.tile_rows = o->tile_rows;
     if (o->tile_nnz) r.tile_nnz = o->tile_nnz;
+    if (o->stages) r.stages = o->stages;
     if (o->timeout_ms) r.timeout_ms = o->timeout_ms;
     r.debug_stall = o->debug_stall;
     return r;
 }
 
-static size_t smem_bytes(int32_t tile_nnz, int32_t tile_rows)
+static size_t smem_bytes(int32_t tile_nnz, int32_t tile_rows, int32_t ns = 2)
 {
-    return (size_t)tile_smem_bytes(tile_nnz, tile_rows);
+    return (size_t)tile_smem_bytes(tile_nnz, tile_rows, ns);
 }
 
 int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t tile_nnz)
@@ -853,6 +875,43 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
             r = e;
         }
     }
+
+    // tiles of the local / remote parts (overlapped engine), same size limits
+    auto cut = [&](const std::vector<int32_t> &rp2, std::vector<Item> &out) {
+        const int64_t n = (int64_t)rp2.size() - 1;
+        int64_t r = 0;
+        while (r < n) {
+            int64_t e = r;
+            while (e < n && e - r < tile_rows && rp2[e + 1] - rp2[r] <= tile_nnz) e++;
+            if (e == r) e = r + 1;
+            Item it{};
+            it.kind = kSpmv;
+            it.b = (int32_t)r;
+            it.e = (int32_t)e;
+            it.k0 = rp2[r];
+            it.k1 = rp2[e];
+            out.push_back(it);
+            r = e;
+        }
+    };
+    std::vector<Item> tl, tr;
+    if (!P->h_rowptrL.empty()) {
+        cut(P->h_rowptrL, tl);
+        cut(P->h_rowptrR, tr);
+    }
+    Item *d_tl = nullptr, *d_tr = nullptr;
+    if (!tl.empty()) {
+        NAP_CUDA(cudaMalloc(&d_tl, sizeof(Item) * tl.size()));
+        NAP_CUDA(cudaMalloc(&d_tr, sizeof(Item) * tr.size()));
+        NAP_CUDA(cudaMemcpy(d_tl, tl.data(), sizeof(Item) * tl.size(), cudaMemcpyHostToDevice));
+        NAP_CUDA(cudaMemcpy(d_tr, tr.data(), sizeof(Item) * tr.size(), cudaMemcpyHostToDevice));
+    }
+    if (S.d_tilesL) cudaFree(S.d_tilesL);
+    if (S.d_tilesR) cudaFree(S.d_tilesR);
+    S.d_tilesL = d_tl;
+    S.d_tilesR = d_tr;
+    S.n_tilesL = (int32_t)tl.size();
+    S.n_tilesR = (int32_t)tr.size();
 
     Item *d_items = nullptr;
     uint64_t *d_cnt = nullptr;
@@ -992,6 +1051,21 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
     return NAPSPMV_OK;
 }
 
+using SpmvKernel = void (*)(Csr3, const double *, const double *, const double *, double *, Scale,
+                            const Item *, int, int, int, int, int *);
+template <bool F32, int MODE>
+static SpmvKernel pick_spmv(int vec)
+{
+    switch (vec) {
+    case 1: return k_spmv<1, F32, MODE>;
+    case 2: return k_spmv<2, F32, MODE>;
+    case 4: return k_spmv<4, F32, MODE>;
+    case 8: return k_spmv<8, F32, MODE>;
+    case 16: return k_spmv<16, F32, MODE>;
+    default: return k_spmv<32, F32, MODE>;
+    }
+}
+
 static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
                           double scale, const napspmv_opts &o, cudaStream_t s, int64_t *kernels)
 {
@@ -1002,7 +1076,7 @@ static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, 
     };
     Csr3 A{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
     using SpmvFn = void (*)(Csr3, const double *, const double *, const double *, double *, Scale,
-                            const Item *, int, int, int, int *);
+                            const Item *, int, int, int, int, int *);
     SpmvFn sp = nullptr;
 #define NAP_CASE(V) \
     case V: sp = f32 ? k_spmv<V, true> : k_spmv<V, false>; break;
@@ -1015,32 +1089,66 @@ static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, 
         NAP_CASE(32)
     }
 #undef NAP_CASE
-    const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows);
+    const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows, o.stages);
     const ItemSet &S = P->items;
     const int n_tiles = S.n_items - S.spmv_first;
+    int occ = 0;
+    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sp, NT, sm));
+    const int sp_grid = std::max(1, std::min(n_tiles, P->num_sms * std::max(occ, 1)));
+    const bool overlap = o.engine == NAPSPMV_ENGINE_OVERLAP && S.n_tilesL > 0;
+    Csr3 AL{P->d_rowptrL, P->d_colL, P->d_valL, f32 ? P->d_val32L : nullptr};
+    Csr3 AR{P->d_rowptrR, P->d_colR, P->d_valR, f32 ? P->d_val32R : nullptr};
+    SpmvFn spL = f32 ? pick_spmv<true, kLocal>(o.vec) : pick_spmv<false, kLocal>(o.vec);
+    SpmvFn spR = f32 ? pick_spmv<true, kRemote>(o.vec) : pick_spmv<false, kRemote>(o.vec);
+    if (overlap) {
+        if (int rc = prepare_smem(spL, sm)) return rc;
+        if (int rc = prepare_smem(spR, sm)) return rc;
+    }
+    // the local part leaves one CTA slot per SM free for the message steps
+    const int gridL = std::max(1, std::min(S.n_tilesL, P->num_sms * std::max(occ - 1, 1)));
+    const int gridR = std::max(1, std::min(S.n_tilesR, P->num_sms * std::max(occ, 1)));
     int64_t nk = 0;
     for (int k = 0; k < reps; k++) {
         const double *x = (k == 0) ? v : (((reps - k) & 1) == 0 ? w : ws->xtmp);
         double *y = (((reps - 1 - k) & 1) == 0) ? w : ws->xtmp;
+        if (overlap) {
+            // Algorithm NAPSpMV: local_spmv(A_on_process) needs no message and
+            // runs on a second stream while the message steps proceed
+            NAP_CUDA(cudaEventRecord(P->ev_fork, s));
+            NAP_CUDA(cudaStreamWaitEvent(P->aux, P->ev_fork, 0));
+            spL<<<gridL, NT, sm, P->aux>>>(AL, x, ws->bll, ws->bnl, y, make_scale(scale),
+                                             S.d_tilesL, S.n_tilesL, o.tile_nnz, o.tile_rows,
+                                             o.stages, ws->err);
+            nk++;
+            NAP_CUDA(cudaEventRecord(P->ev_join, P->aux));
+        }
         if (P->n_bll + P->n_lbuf > 0) {
             k_gather2<<<grid(P->n_bll + P->n_lbuf), NT, 0, s>>>(
                 x, P->lists[L_BLL].d_idx, ws->bll, (int)P->n_bll, P->lists[L_LBUF].d_idx, ws->lbuf,
-                (int)P->n_lbuf);
+                (int)P->n_lbuf, ws->err);
             nk++;
         }
         if (P->n_gs > 0) {
-            k_pack<<<grid(P->n_gs), NT, 0, s>>>(x, ws->lbuf, P->d_pack_src, ws->gsend, (int)P->n_gs);
+            k_pack<<<grid(P->n_gs), NT, 0, s>>>(x, ws->lbuf, P->d_pack_src, ws->gsend, (int)P->n_gs,
+                                                ws->err);
             k_transfer<<<grid(P->n_gs), NT, 0, s>>>(ws->gsend, P->d_xfer_dst, ws->grecv,
-                                                    (int)P->n_gs);
+                                                    (int)P->n_gs, ws->err);
             nk += 2;
         }
         if (P->n_bnl > 0) {
-            k_unpack<<<grid(P->n_bnl), NT, 0, s>>>(ws->grecv, P->d_unp_src, ws->bnl, (int)P->n_bnl);
+            k_unpack<<<grid(P->n_bnl), NT, 0, s>>>(ws->grecv, P->d_unp_src, ws->bnl, (int)P->n_bnl,
+                                                   ws->err);
             nk++;
         }
-        sp<<<std::max(1, std::min(n_tiles, P->num_sms * 4)), NT, sm, s>>>(
-            A, x, ws->bll, ws->bnl, y, make_scale(scale), S.d_items + S.spmv_first, n_tiles,
-            o.tile_nnz, o.tile_rows, ws->err);
+        if (overlap) {
+            NAP_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
+            spR<<<gridR, NT, sm, s>>>(AR, x, ws->bll, ws->bnl, y, make_scale(scale), S.d_tilesR,
+                                      S.n_tilesR, o.tile_nnz, o.tile_rows, o.stages, ws->err);
+        } else {
+            sp<<<sp_grid, NT, sm, s>>>(A, x, ws->bll, ws->bnl, y, make_scale(scale),
+                                       S.d_items + S.spmv_first, n_tiles, o.tile_nnz,
+                                       o.tile_rows, o.stages, ws->err);
+        }
         nk++;
         NAP_CUDA(cudaGetLastError());
     }
@@ -1055,7 +1163,7 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
 {
     {
         const bool f32 = o.precision == NAPSPMV_PREC_F32;
-        const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows);
+        const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows, o.stages);
         int rc = NAPSPMV_OK;
 #define NAP_CASE(V)                                                                  \
     case V: rc = f32 ? prepare_smem(k_spmv<V, true>, sm) : prepare_smem(k_spmv<V, false>, sm); \
@@ -1127,12 +1235,19 @@ static int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
         set_error(NAPSPMV_ERR_STATE, "plan was built without NAPSPMV_F32_VALUES");
         return NAPSPMV_ERR_STATE;
     }
-    if (o.engine != NAPSPMV_ENGINE_FUSED && o.engine != NAPSPMV_ENGINE_PHASED) {
+    if (o.engine != NAPSPMV_ENGINE_FUSED && o.engine != NAPSPMV_ENGINE_PHASED &&
+        o.engine != NAPSPMV_ENGINE_OVERLAP) {
         set_error(NAPSPMV_ERR_ARG, "unknown engine");
         return NAPSPMV_ERR_ARG;
     }
     if (o.timeout_ms < 1) {
         set_error(NAPSPMV_ERR_ARG, "timeout_ms must be >= 1");
+        return NAPSPMV_ERR_ARG;
+    }
+    if (o.stages < 2 || o.stages > kMaxStages ||
+        smem_bytes(o.tile_nnz, o.tile_rows, o.stages) > 220 * 1024) {
+        set_error(NAPSPMV_ERR_ARG, "stages must be 2..4 and all stages must fit in 220 KiB of "
+                                   "shared memory");
         return NAPSPMV_ERR_ARG;
     }
     return NAPSPMV_OK;
@@ -1185,7 +1300,7 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
         }
     }
     if (!rc) {
-        if (count == 1 && o.engine == NAPSPMV_ENGINE_PHASED)
+        if (count == 1 && (o.engine == NAPSPMV_ENGINE_PHASED || o.engine == NAPSPMV_ENGINE_OVERLAP))
             rc = launch_phased(P0, ws && ws[0] ? ws[0] : P0->ws, v[0], w[0], reps[0],
                                scale ? scale[0] : 1.0, o, s);
         else if (count == 1)
@@ -1299,4 +1414,54 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
     view.err = nullptr;  // nothing of the view is freed
     if (cur != P->device) cudaSetDevice(cur);
     return rc;
+}
+
+// The three-block SpMV step alone (phase 5 / local_spmv over the three blocks),
+// on the receive buffers the workspace holds from its last apply.
+extern "C" int napspmv_spmv_step(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w,
+                                 double scale, const napspmv_opts *opts, void *stream)
+{
+    using namespace nap;
+    if (!P || !v || !w || (const double *)w == v) {
+        set_error(NAPSPMV_ERR_ARG, "NULL plan or vector, or w == v");
+        return NAPSPMV_ERR_ARG;
+    }
+    napspmv_ws_t *W = ws ? ws : P->ws;
+    napspmv_opts o = resolve_opts(P, opts);
+    int rc = check_opts(P, o);
+    if (rc) return rc;
+    int cur = 0;
+    NAP_CUDA(cudaGetDevice(&cur));
+    if (cur != P->device) NAP_CUDA(cudaSetDevice(P->device));
+    if ((rc = build_items(P, o.chunk, o.tile_rows, o.tile_nnz))) return rc;
+    const bool f32 = o.precision == NAPSPMV_PREC_F32;
+    Csr3 A{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
+    using SpmvFn = void (*)(Csr3, const double *, const double *, const double *, double *, Scale,
+                            const Item *, int, int, int, int, int *);
+    SpmvFn sp = nullptr;
+#define NAP_CASE(V) \
+    case V: sp = f32 ? k_spmv<V, true> : k_spmv<V, false>; break;
+    switch (o.vec) {
+        NAP_CASE(1)
+        NAP_CASE(2)
+        NAP_CASE(4)
+        NAP_CASE(8)
+        NAP_CASE(16)
+        NAP_CASE(32)
+    }
+#undef NAP_CASE
+    const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows, o.stages);
+    if ((rc = prepare_smem(sp, sm))) return rc;
+    const ItemSet &S = P->items;
+    const int n_tiles = S.n_items - S.spmv_first;
+    int occ = 0;
+    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sp, NT, sm));
+    sp<<<std::max(1, std::min(n_tiles, P->num_sms * std::max(occ, 1))), NT, sm,
+         (cudaStream_t)stream>>>(A, v, W->bll, W->bnl, w, make_scale(scale),
+                                 S.d_items + S.spmv_first, n_tiles, o.tile_nnz, o.tile_rows,
+                                 o.stages, W->err);
+    count_launch(1);
+    NAP_CUDA(cudaGetLastError());
+    if (cur != P->device) cudaSetDevice(cur);
+    return NAPSPMV_OK;
 }

@@ -62,6 +62,8 @@ struct ItemSet {
     int32_t chunk = 0, tile_rows = 0, tile_nnz = 0;
     int32_t n_items = 0;
     int32_t spmv_first = 0;  // items [spmv_first, n_items) are the row tiles
+    Item *d_tilesL = nullptr, *d_tilesR = nullptr;  // tiles of the split parts
+    int32_t n_tilesL = 0, n_tilesR = 0;
     Item *d_items = nullptr;
     // per-apply increments of every counter, [kNumCounters][nn]
     uint64_t *d_cnt = nullptr;
@@ -106,6 +108,18 @@ struct napspmv_plan_s {
     uint32_t *d_colenc = nullptr;
     double *d_val = nullptr;
     float *d_val32 = nullptr;
+
+    // the same matrix split in two CSR parts for the overlapped engine: the
+    // on_process entries (L, columns index v) and the on_node + off_node
+    // entries (R, columns coded by block); each row keeps its stored order
+    int64_t nnzL = 0, nnzR = 0;
+    int32_t *d_rowptrL = nullptr, *d_rowptrR = nullptr;
+    uint32_t *d_colL = nullptr, *d_colR = nullptr;
+    double *d_valL = nullptr, *d_valR = nullptr;
+    float *d_val32L = nullptr, *d_val32R = nullptr;
+    std::vector<int32_t> h_rowptrL, h_rowptrR;
+    cudaStream_t aux = nullptr;  // low-priority stream of the local SpMV
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // sizes of the buffers and index arrays of the message steps
     int64_t n_bll = 0, n_lbuf = 0, n_gs = 0, n_bnl = 0;

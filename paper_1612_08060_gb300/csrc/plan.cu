@@ -353,6 +353,41 @@ __global__ void k_three_block(const int64_t *rp, int64_t n, const int32_t *col, 
     }
 }
 
+// Lengths of every row's on_process part (L) and remote part (R); the entry
+// after the last row is 0 so that an exclusive scan ends with the totals.
+__global__ void k_split_lens(const int32_t *split, int64_t n, int32_t *lenL, int32_t *lenR)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        lenL[i] = i < n ? split[3 * i] : 0;
+        lenR[i] = i < n ? split[3 * i + 1] + split[3 * i + 2] : 0;
+    }
+}
+
+// Copies each three-block row into its L part (the first split[3i] entries)
+// and R part (the rest), keeping the order.
+__global__ void k_split_copy(const int32_t *rp, int64_t n, const uint32_t *col, const double *val,
+                             const float *val32, const int32_t *rpL, const int32_t *rpR,
+                             uint32_t *colL, double *valL, float *val32L, uint32_t *colR,
+                             double *valR, float *val32R)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = rp[i], nl = rpL[i + 1] - rpL[i], e = rp[i + 1];
+        for (int32_t k = 0; k < nl; k++) {
+            colL[rpL[i] + k] = col[b + k];
+            valL[rpL[i] + k] = val[b + k];
+            if (val32L) val32L[rpL[i] + k] = val32[b + k];
+        }
+        for (int32_t k = b + nl; k < e; k++) {
+            const int32_t q = rpR[i] + (k - b - nl);
+            colR[q] = col[k];
+            valR[q] = val[k];
+            if (val32R) val32R[q] = val32[k];
+        }
+    }
+}
+
 // ------------------------------------------------------------ CUB helpers
 
 struct Cub {
@@ -822,6 +857,53 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
                                          P->d_val32, P->d_split, P->d_rowptr, bad.p);
     CK(cudaGetLastError());
     check_bad(bad, "internal: column missing from its receive buffer");
+
+    // ---- local / remote split
+    {
+        dvec<int32_t> lenL(n + 1), lenR(n + 1);
+        CK(cudaMalloc(&P->d_rowptrL, sizeof(int32_t) * (n + 16)));
+        CK(cudaMalloc(&P->d_rowptrR, sizeof(int32_t) * (n + 16)));
+        CK(cudaMemset(P->d_rowptrL, 0, sizeof(int32_t) * (n + 16)));
+        CK(cudaMemset(P->d_rowptrR, 0, sizeof(int32_t) * (n + 16)));
+        k_split_lens<<<blocks_for(n + 1), 256>>>(P->d_split, n, lenL.p, lenR.p);
+        CK(cudaGetLastError());
+        size_t b = 0;
+        CK(cub::DeviceScan::ExclusiveSum(nullptr, b, lenL.p, P->d_rowptrL, (int)(n + 1)));
+        void *tmp = cb.temp(b);
+        CK(cub::DeviceScan::ExclusiveSum(tmp, b, lenL.p, P->d_rowptrL, (int)(n + 1)));
+        CK(cub::DeviceScan::ExclusiveSum(tmp, b, lenR.p, P->d_rowptrR, (int)(n + 1)));
+        P->h_rowptrL.resize(n + 1);
+        P->h_rowptrR.resize(n + 1);
+        CK(cudaMemcpy(P->h_rowptrL.data(), P->d_rowptrL, sizeof(int32_t) * (n + 1),
+                      cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(P->h_rowptrR.data(), P->d_rowptrR, sizeof(int32_t) * (n + 1),
+                      cudaMemcpyDeviceToHost));
+        P->nnzL = P->h_rowptrL[n];
+        P->nnzR = P->h_rowptrR[n];
+        const bool f32 = P->d_val32 != nullptr;
+        auto al = [&](int64_t m, size_t sz) {
+            void *q = nullptr;
+            CK(cudaMalloc(&q, sz * (size_t)std::max<int64_t>(m, 1) + 64));
+            return q;
+        };
+        P->d_colL = (uint32_t *)al(P->nnzL, 4);
+        P->d_valL = (double *)al(P->nnzL, 8);
+        P->d_colR = (uint32_t *)al(P->nnzR, 4);
+        P->d_valR = (double *)al(P->nnzR, 8);
+        if (f32) {
+            P->d_val32L = (float *)al(P->nnzL, 4);
+            P->d_val32R = (float *)al(P->nnzR, 4);
+        }
+        k_split_copy<<<blocks_for(n), 256>>>(P->d_rowptr, n, P->d_colenc, P->d_val, P->d_val32,
+                                             P->d_rowptrL, P->d_rowptrR, P->d_colL, P->d_valL,
+                                             P->d_val32L, P->d_colR, P->d_valR, P->d_val32R);
+        CK(cudaGetLastError());
+        int lo = 0, hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CK(cudaStreamCreateWithPriority(&P->aux, cudaStreamNonBlocking, lo));
+        CK(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    }
     CK(cudaDeviceSynchronize());
 
     // ---- per-node ranges for cutting work items
@@ -878,7 +960,12 @@ void plan_free(napspmv_plan_t *P)
         if (L.d_idx) cudaFree(L.d_idx);
     void *ptrs[] = {P->d_split, P->d_rowptr, P->d_colenc, P->d_val, P->d_val32, P->d_pack_src,
                     P->d_xfer_dst, P->d_unp_src, P->d_gs_msg_off, P->d_gs_msg_dstnode,
-                    P->items.d_items, P->items.d_cnt};
+                    P->items.d_items, P->items.d_cnt, P->items.d_tilesL, P->items.d_tilesR,
+                    P->d_rowptrL, P->d_rowptrR, P->d_colL, P->d_colR, P->d_valL, P->d_valR,
+                    P->d_val32L, P->d_val32R};
+    if (P->aux) cudaStreamDestroy(P->aux);
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -924,15 +1011,20 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         // defaults: lanes per row from the mean row length
         double avg = (double)P->nnz / (double)P->n;
         // rows are summed from shared memory; one lane per row keeps exactly one
-        // FP64 FMA per stored entry (GB300's FP64 pipe is the scarce unit)
-        int vec = avg <= 48 ? 1 : avg <= 192 ? 8 : 32;
+        // FP64 FMA per stored entry (GB300's FP64 pipe is the scarce unit).
+        // (measured on the 128^3 7-point workload: two stages of 2048 entries
+        // beat deeper pipelines, which cost CTAs per SM)
+        int vec = avg <= 16 ? 1 : avg <= 32 ? 2 : avg <= 96 ? 4 : avg <= 384 ? 16 : 32;
+        int rows = 512 / vec;
+        int cap = 2048;
         P->defaults.precision = NAPSPMV_PREC_F64;
-        P->defaults.engine = NAPSPMV_ENGINE_FUSED;
+        P->defaults.engine = NAPSPMV_ENGINE_OVERLAP;
         P->defaults.vec = vec;
         P->defaults.ctas_per_sm = 0;  // occupancy maximum
         P->defaults.chunk = 4096;
-        P->defaults.tile_rows = 512;
-        P->defaults.tile_nnz = 2048;
+        P->defaults.tile_rows = rows;
+        P->defaults.tile_nnz = cap;
+        P->defaults.stages = 2;
         P->defaults.timeout_ms = 10000;
         P->defaults.debug_stall = 0;
         rc = build_items(P, P->defaults.chunk, P->defaults.tile_rows, P->defaults.tile_nnz);

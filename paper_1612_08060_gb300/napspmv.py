@@ -19,7 +19,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = 0, -1,
 HOST, DEVICE = 0, 1
 F32_VALUES, MAP_TEXT = 1, 2
 PREC_F64, PREC_F32 = 0, 1
-ENGINE_FUSED, ENGINE_PHASED = 0, 1
+ENGINE_DEFAULT, ENGINE_FUSED, ENGINE_PHASED, ENGINE_OVERLAP = 0, 1, 2, 3
 (LIST_STD, LIST_NODE, LIST_INTER, LIST_J0, LIST_J1, LIST_J2, LIST_BLL, LIST_BNL, LIST_LBUF,
  LIST_TU, LIST_SPLIT) = range(11)
 
@@ -38,7 +38,8 @@ class napspmv_csr(C.Structure):
 class napspmv_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("engine", C.c_int32), ("vec", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("chunk", C.c_int32), ("tile_rows", C.c_int32),
-                ("tile_nnz", C.c_int32), ("timeout_ms", C.c_int32), ("debug_stall", C.c_int32)]
+                ("tile_nnz", C.c_int32), ("stages", C.c_int32), ("timeout_ms", C.c_int32),
+                ("debug_stall", C.c_int32)]
 
 
 STAT_FIELDS = [
@@ -89,6 +90,8 @@ def lib():
                                            C.POINTER(napspmv_opts), _VP]),
             "napspmv_apply_host": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_double, _VP]),
             "napspmv_apply_noalloc": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_double, _VP]),
+            "napspmv_spmv_step": (C.c_int, [_VP, _VP, _VP, _VP, C.c_double,
+                                            C.POINTER(napspmv_opts), _VP]),
             "napspmv_apply_batch": (C.c_int, [C.c_int32, C.POINTER(_VP), C.POINTER(_VP),
                                               C.POINTER(_VP), C.POINTER(_VP),
                                               C.POINTER(C.c_int32), C.POINTER(C.c_double),
@@ -236,6 +239,13 @@ def napspmv_apply_noalloc(plan, v, w, reps=1, scale=1.0, stream=None):
     """As napspmv_apply_n, with no allocation (scratch in a fixed device array)."""
     _check(lib().napspmv_apply_noalloc(plan.handle, _dptr(v), _dptr(w), int(reps), float(scale),
                                        _stream(stream)))
+
+
+def napspmv_spmv_step(plan, v, w, scale=1.0, opts=None, ws=None, stream=None):
+    """The three-block SpMV step alone, on the workspace's current receive buffers."""
+    _check(lib().napspmv_spmv_step(plan.handle, ws.handle if ws else None, _dptr(v), _dptr(w),
+                                   float(scale), C.byref(opts) if opts else None,
+                                   _stream(stream)))
 
 
 def napspmv_apply_host(plan, v_host, w_host, reps=1, scale=1.0, stream=None):

@@ -64,7 +64,8 @@ class Request:
 
 class Server:
     def __init__(self, mem_budget=None, max_active=64, iters_per_step=8, rtol=1e-10,
-                 inner_rtol=1e-4, max_outer=40, max_inner=200000, device=None, keep_results=False):
+                 inner_rtol=1e-4, max_outer=40, max_inner=200000, device=None, keep_results=False,
+                 cache=None):
         self.dev = torch.device(device or "cuda")
         free, _ = torch.cuda.mem_get_info(self.dev)
         self.budget = int(mem_budget if mem_budget else 0.5 * free)
@@ -74,7 +75,10 @@ class Server:
         self.max_outer, self.max_inner = max_outer, max_inner
         self.keep = keep_results
         self.stream = torch.cuda.Stream(self.dev)
-        self.cache: "collections.OrderedDict[str, Matrix]" = collections.OrderedDict()
+        # plans may be shared between servers (a warm cache): their bytes are
+        # then counted by whoever built them
+        self.cache: "collections.OrderedDict[str, Matrix]" = (
+            cache if cache is not None else collections.OrderedDict())
         self.mem_used = 0
         self.steps = 0
         self.batch_sizes = []
@@ -248,3 +252,41 @@ def summarize(reqs, wall_s):
             "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3)}
+
+
+def warm_cache(specs, device=None):
+    """Build (once) the plan of every matrix the requests use."""
+    srv = Server(max_active=1, device=device)
+    t0 = time.perf_counter()
+    for sp in specs:
+        srv._matrix(sp)
+    return srv.cache, time.perf_counter() - t0
+
+
+def compare(count=512, n_lo=1e3, n_hi=2e5, seed=1239, load=0.8, device=None):
+    """Continuous batching vs the plain per-request loop on the same requests.
+
+    The plain loop's saturated throughput (all requests queued at once) sets the
+    arrival rate lambda = load * throughput; both loops then serve the same
+    Poisson arrivals in real time.  Plans are built beforehand and shared."""
+    base = inputs.serving_requests(count, 1.0, seed, n_lo=n_lo, n_hi=n_hi)
+    cache, build_s = warm_cache(base, device)
+    t0 = time.perf_counter()
+    plain_sat = Server(max_active=1, cache=cache, device=device).run(base, realtime=False)
+    sat_s = time.perf_counter() - t0
+    rate = load * count / sat_s
+    specs = inputs.serving_requests(count, rate, seed, n_lo=n_lo, n_hi=n_hi)
+    out = {"requests": count, "n_range": [n_lo, n_hi], "rate_hz": rate,
+           "plan_build_s": build_s, "plain_saturated_rps": count / sat_s,
+           "mix": {"spmv": sum(r["kind"] == "spmv" for r in specs),
+                   "cg": sum(r["kind"] == "cg" for r in specs)},
+           "tolerance": "SpMV FP64 <= 1e-13 normwise; CG-IR ||b - Ax|| / ||b|| <= 1e-10"}
+    for name, act in (("batched", 64), ("plain", 1)):
+        srv = Server(max_active=act, cache=cache, device=device)
+        t0 = time.perf_counter()
+        reqs = srv.run(specs, realtime=True)
+        wall = time.perf_counter() - t0
+        out[name] = summarize(reqs, wall)
+        out[name]["mean_batch"] = float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0
+    del plain_sat
+    return out

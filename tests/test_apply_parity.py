@@ -24,7 +24,8 @@ def run(plan, v, reps=1, scale=1.0, **opts):
     return wd.cpu().numpy()
 
 
-ENGINES = [dict(engine=nap.ENGINE_FUSED), dict(engine=nap.ENGINE_PHASED)]
+ENGINES = [dict(engine=nap.ENGINE_FUSED), dict(engine=nap.ENGINE_PHASED),
+           dict(engine=nap.ENGINE_OVERLAP)]
 SHAPES = [dict(vec=v) for v in (1, 2, 4, 8, 32)]
 
 
@@ -110,14 +111,18 @@ def test_edge_cases(eng):
         assert_close_fp64(w, O.spmv(D.row_ptr, D.col, D.val, v), abs_row_bound(D, v))
 
 
-def test_engines_agree_bitwise():
-    """Both engines evaluate every row in the same order: identical bits."""
+@pytest.mark.parametrize("reps", [1, 3])
+def test_engines_agree_bitwise(reps):
+    """With one lane per row every engine evaluates each row's FMA chain in the
+    same order (on_process, on_node, off_node; the overlapped engine continues
+    the chain from the local partial): identical bits."""
     A = I.aniso_q1(64)
     v = I.vector(A.n, 21)
     plan = gpu_plan(A, 16, 4)
-    a = run(plan, v, engine=nap.ENGINE_FUSED, vec=4)
-    b = run(plan, v, engine=nap.ENGINE_PHASED, vec=4)
-    assert np.array_equal(a, b)
+    a = run(plan, v, reps=reps, scale=0.25, engine=nap.ENGINE_FUSED, vec=1)
+    b = run(plan, v, reps=reps, scale=0.25, engine=nap.ENGINE_PHASED, vec=1)
+    c = run(plan, v, reps=reps, scale=0.25, engine=nap.ENGINE_OVERLAP, vec=1)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
 def test_host_entry_point():

@@ -25,7 +25,7 @@ def test_batch_equals_alone():
     outs = [torch.full_like(v, float("nan")) for v in vs]
     reps = [m[3] for m in mats]
     scales = [m[4] for m in mats]
-    opts = nap.make_opts(vec=4)
+    opts = nap.make_opts(engine=nap.ENGINE_FUSED, vec=4)  # the batched launch's engine
     nap.napspmv_apply_batch(plans, vs, outs, reps, scales, opts=opts, ws=wss)
     assert nap.napspmv_status(plans[0]) == 0
     assert nap.napspmv_ws_status(wss[4]) == 0

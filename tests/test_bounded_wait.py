@@ -20,7 +20,7 @@ def test_stalled_wait_times_out_and_recovers():
     v = I.vector(A.n, 1)
     vd = torch.from_numpy(v).cuda()
     wd = torch.empty_like(vd)
-    nap.napspmv_apply_ex(plan, vd, wd, 3, 1.0, nap.make_opts(debug_stall=1, timeout_ms=100))
+    nap.napspmv_apply_ex(plan, vd, wd, 3, 1.0, nap.make_opts(engine=nap.ENGINE_FUSED, debug_stall=1, timeout_ms=100))
     assert nap.napspmv_status(plan) == nap.ERR_TIMEOUT
     assert nap.napspmv_status(plan) == nap.OK  # the status was cleared
     nap.napspmv_apply(plan, vd, wd)
@@ -33,9 +33,10 @@ def test_sticky_error_skips_work_until_cleared():
     plan = gpu_plan(A, 4, 2)
     vd = torch.ones(A.n, dtype=torch.float64, device="cuda")
     wd = torch.full_like(vd, 7.0)
-    nap.napspmv_apply_ex(plan, vd, wd, 1, 1.0, nap.make_opts(debug_stall=1, timeout_ms=50))
+    nap.napspmv_apply_ex(plan, vd, wd, 1, 1.0, nap.make_opts(engine=nap.ENGINE_FUSED, debug_stall=1, timeout_ms=50))
     torch.cuda.synchronize()
     w2 = torch.full_like(vd, 7.0)
-    nap.napspmv_apply(plan, vd, w2)  # sees the sticky flag and does no work
+    nap.napspmv_apply(plan, vd, w2)  # (default engine) sees the sticky flag, does no work
+    nap.napspmv_apply_ex(plan, vd, w2, 2, 1.0, nap.make_opts(engine=nap.ENGINE_FUSED))
     assert nap.napspmv_status(plan) == nap.ERR_TIMEOUT
     assert torch.all(w2 == 7.0)
