@@ -1,8 +1,9 @@
 """Launch-option autotuner for the node-aware apply.
 
-Searches lanes per row (``vec``), the SpMV tile shape (``tile_rows``,
-``tile_nnz`` = shared-memory staging of the products), the gather chunk of the
-message steps (``chunk``) and CTAs per SM by coordinate descent: starting from the
+Searches the engine (overlapped, phased, fused), lanes per row (``vec``), the
+SpMV tile shape (``tile_rows``, ``tile_nnz``: the entries one shared-memory
+stage holds), the pipeline depth (``stages``) and the gather chunk of the fused
+engine's message items (``chunk``) by coordinate descent: starting from the
 plan's defaults, each parameter in turn is set to each candidate while the
 others stay fixed, the fastest is kept, and the sweep repeats until nothing
 improves.  Each candidate is timed with CUDA events over chained applies
@@ -20,11 +21,12 @@ import numpy as np
 from . import napspmv as nap
 
 CANDIDATES = {
-    "vec": [1, 2, 4, 8, 16],
-    "tile_nnz": [2048, 4096, 8192],
-    "tile_rows": [256, 512, 1024, 2048],
-    "chunk": [1024, 2048, 4096, 8192, 16384],
-    "ctas_per_sm": [2, 3, 4, 5],
+    "engine": [nap.ENGINE_OVERLAP, nap.ENGINE_PHASED, nap.ENGINE_FUSED],
+    "vec": [1, 2, 4, 8],
+    "tile_nnz": [1024, 1536, 2048, 3072],
+    "tile_rows": [256, 384, 512, 1024],
+    "stages": [2, 3],
+    "chunk": [2048, 4096, 8192],
 }
 
 _cache: dict = {}
@@ -68,14 +70,12 @@ def tune(plan, row_ptr, precision=nap.PREC_F64, reps=20, max_sweeps=2, cache_fil
         return best, _cache[key]["ms"]
     d = nap.napspmv_get_default_opts(plan)
     cur = {k: int(getattr(d, k)) for k in CANDIDATES}
-    if cur["ctas_per_sm"] == 0:
-        cur["ctas_per_sm"] = 5
     v = torch.rand(plan.n, dtype=torch.float64, device="cuda") * 2 - 1
     w = torch.empty_like(v)
 
     def measure(c):
         try:
-            o = nap.make_opts(precision=precision, engine=nap.ENGINE_FUSED, **c)
+            o = nap.make_opts(precision=precision, **c)
             return time_opts(plan, v, w, o, reps=reps)
         except nap.NapError:
             return float("inf")
