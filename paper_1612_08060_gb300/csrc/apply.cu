@@ -83,6 +83,39 @@ __device__ __forceinline__ float ld_stream_f32(const float *p)
     asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
+// L2 cache policies: streams read once (matrix, index arrays) are evicted
+// first, so the gathered vectors (v, b_{l->l}, b_{nl->l}) stay L2-resident.
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ double ld_keep_f64(const double *p, uint64_t pol)
+{
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_stream_hint_s32(const int32_t *p, uint64_t pol)
+{
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_hint_u32(const uint32_t *p, uint64_t pol)
+{
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 __device__ __forceinline__ long long globaltimer()
 {
     long long t;
@@ -99,7 +132,7 @@ template <bool INKERNEL>
 __device__ __forceinline__ double ldx(const double *p)
 {
     if (INKERNEL) return *p;
-    return __ldg(p);
+    return ld_keep_f64(p, policy_evict_last());
 }
 
 // Batched element loop over [b, e): U independent index loads, then U
@@ -236,10 +269,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
+    const uint64_t pol = policy_evict_first();  // the matrix is streamed once per apply
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], "
+        "%2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
         : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
@@ -555,8 +589,9 @@ template <bool INKERNEL, int U>
 __device__ __noinline__ void step_gather(double *dst, const double *src, const int32_t *idx,
                                             int b, int e, int tid)
 {
+    const uint64_t pol = policy_evict_first();
     batched<U>(
-        b, e, tid, [&](int k) { return (uint32_t)ld_stream_s32(idx + k); },
+        b, e, tid, [&](int k) { return (uint32_t)ld_stream_hint_s32(idx + k, pol); },
         [&](int, uint32_t j) { return ldx<INKERNEL>(src + j); },
         [&](int k, uint32_t, double v) { dst[k] = v; });
 }
@@ -564,8 +599,9 @@ template <bool INKERNEL, int U>
 __device__ __noinline__ void step_pack(double *gsend, const double *x, const double *lbuf,
                                           const uint32_t *src, int b, int e, int tid)
 {
+    const uint64_t pol = policy_evict_first();
     batched<U>(
-        b, e, tid, [&](int k) { return ld_stream_u32(src + k); },
+        b, e, tid, [&](int k) { return ld_stream_hint_u32(src + k, pol); },
         [&](int, uint32_t u) {
             return (u & kFromLbuf) ? ldx<INKERNEL>(lbuf + (u & ~kFromLbuf)) : ldx<INKERNEL>(x + u);
         },
@@ -575,8 +611,9 @@ template <bool INKERNEL, int U>
 __device__ __noinline__ void step_transfer(double *grecv, const double *gsend,
                                               const int32_t *dst, int b, int e, int tid)
 {
+    const uint64_t pol = policy_evict_first();
     batched<U>(
-        b, e, tid, [&](int k) { return (uint32_t)ld_stream_s32(dst + k); },
+        b, e, tid, [&](int k) { return (uint32_t)ld_stream_hint_s32(dst + k, pol); },
         [&](int k, uint32_t) { return ldx<INKERNEL>(gsend + k); },
         [&](int, uint32_t d, double v) { grecv[d] = v; });
 }
