@@ -224,6 +224,7 @@ def main():
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--tile-nnz", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--pipeline", default="default", choices=["default", "cta", "warp"])
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -273,6 +274,8 @@ def main():
                                  "overlap": nap.ENGINE_OVERLAP}[args.engine],
                          vec=args.vec, chunk=args.chunk, tile_rows=args.tile_rows,
                          tile_nnz=args.tile_nnz, stages=args.stages,
+                         pipeline={"default": 0, "cta": nap.PIPELINE_CTA,
+                                   "warp": nap.PIPELINE_WARP}[args.pipeline],
                          precision=nap.PREC_F32 if args.precision == "f32" else nap.PREC_F64,
                          ctas_per_sm=args.ctas_per_sm)
     eff = nap.napspmv_get_default_opts(plan)
@@ -376,6 +379,7 @@ def main():
                    "tile_rows": opts.tile_rows or eff.tile_rows,
                    "tile_nnz": opts.tile_nnz or eff.tile_nnz,
                    "stages": opts.stages or eff.stages,
+                   "pipeline": {1: "cta", 2: "warp"}[opts.pipeline or eff.pipeline],
                    "l2": "inputs larger than L2: each apply streams the 175 MB col/val "
                          "arrays (L2 129 MB); not flushed between steps",
                    "parallelism": f"replicas{ws}"},

@@ -83,6 +83,9 @@ extern "C" {
                                     each row's sum (with vec = 1 the same
                                     bits as PHASED and FUSED)                */
 
+#define NAPSPMV_PIPELINE_CTA 1
+#define NAPSPMV_PIPELINE_WARP 2
+
 typedef struct napspmv_plan_s napspmv_plan_t;
 typedef struct napspmv_ws_s napspmv_ws_t;
 
@@ -114,6 +117,11 @@ typedef struct {
                             single row gets a tile of its own                  */
     int32_t stages;      /* shared-memory stages of the phased SpMV pipeline
                             (2..4; the fused engine always uses 2)             */
+    int32_t pipeline;    /* SpMV tiles of the phased / overlapped engines:
+                            NAPSPMV_PIPELINE_CTA (a CTA per tile) or
+                            NAPSPMV_PIPELINE_WARP (each warp its own stages and
+                            tiles of tile_rows / 8 rows, tile_nnz / 8 entries);
+                            a CTA takes a contiguous run of tiles either way */
     int32_t timeout_ms;  /* limit of every device-side wait                    */
     int32_t debug_stall; /* test hook (fused engine): 1 makes the first work
                             item wait on a counter nothing increments, so the

@@ -2,8 +2,9 @@
 
 Searches the engine (overlapped, phased, fused), lanes per row (``vec``), the
 SpMV tile shape (``tile_rows``, ``tile_nnz``: the entries one shared-memory
-stage holds), the pipeline depth (``stages``) and the gather chunk of the fused
-engine's message items (``chunk``) by coordinate descent: starting from the
+stage holds), the pipeline depth (``stages``), CTA or warp tiles (``pipeline``)
+and the gather chunk of the fused engine's message items (``chunk``) by
+coordinate descent: starting from the
 plan's defaults, each parameter in turn is set to each candidate while the
 others stay fixed, the fastest is kept, and the sweep repeats until nothing
 improves.  Each candidate is timed with CUDA events over chained applies
@@ -26,6 +27,7 @@ CANDIDATES = {
     "tile_nnz": [1024, 1536, 2048, 3072],
     "tile_rows": [256, 384, 512, 1024],
     "stages": [2, 3],
+    "pipeline": [nap.PIPELINE_CTA, nap.PIPELINE_WARP],
     "chunk": [2048, 4096, 8192],
 }
 
@@ -101,3 +103,33 @@ def tune(plan, row_ptr, precision=nap.PREC_F64, reps=20, max_sweeps=2, cache_fil
         with open(cache_file, "w") as f:
             json.dump(_cache, f, indent=1)
     return cur, best_ms
+
+
+def main(argv=None):
+    """python -m paper_1612_08060_gb300.autotune --config K: tune workload K
+    (see inputs.workload) and print each candidate's time and the winner."""
+    import argparse
+
+    import torch
+
+    from . import inputs
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--scale-down", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--cache", default=None)
+    a = ap.parse_args(argv)
+    w = inputs.workload(a.config, a.scale_down)
+    A = w.build()
+    plan = nap.napspmv_plan(A.row_ptr, A.col, A.val, w.n_p, w.ppn, nap.F32_VALUES)
+    torch.cuda.synchronize()
+    prec = nap.PREC_F32 if a.precision == "f32" else nap.PREC_F64
+    best, ms = tune(plan, A.row_ptr, precision=prec, reps=a.reps, cache_file=a.cache,
+                    verbose=True)
+    print(json.dumps({"workload": w.name, "precision": a.precision, "best": best,
+                      "ms_per_apply": ms}))
+
+
+if __name__ == "__main__":
+    main()

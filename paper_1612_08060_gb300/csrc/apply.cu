@@ -774,22 +774,24 @@ __global__ void __launch_bounds__(NT)
     tile_smem_init(smem, ns);
     double *red = tile_red(smem, cap, trows, ns);
     uint32_t phase = 0;
-    const int G = gridDim.x;
-    // tiles q = blockIdx.x + i G, i = 0, 1, ...; tile i uses stage i % ns and is
-    // requested ns - 1 tiles ahead
+    // a contiguous block of tiles per CTA (neighbouring rows share x and the
+    // receive buffers of their process, which then stay in this SM's L1);
+    // tile i of the block uses stage i % ns and is requested ns - 1 tiles ahead
+    const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+    const int q0 = blockIdx.x * per, q1 = min(n_tiles, q0 + per);
     if (tid == 0)
         for (int i = 0; i < ns - 1; i++) {
-            const int q = blockIdx.x + i * G;
-            if (q >= n_tiles) break;
+            const int q = q0 + i;
+            if (q >= q1) break;
             const Item it = tiles[q];
             if (staged_tile(it, cap))
                 tile_issue<F32>(A, tile_stage(smem, i, cap, trows), it.b, it.e, it.k0, it.k1);
         }
     int cur = 0;
-    for (int i = 0, q = blockIdx.x; q < n_tiles; i++, q += G) {
+    for (int i = 0, q = q0; q < q1; i++, q++) {
         const Item it = tiles[q];
-        const int qa = q + (ns - 1) * G;
-        if (tid == 0 && qa < n_tiles) {
+        const int qa = q + (ns - 1);
+        if (tid == 0 && qa < q1) {
             const Item ita = tiles[qa];
             const int sa = (cur + ns - 1) % ns;  // the stage tile i - 1 used
             if (staged_tile(ita, cap))
@@ -805,6 +807,122 @@ __global__ void __launch_bounds__(NT)
         }
         cur = cur + 1 == ns ? 0 : cur + 1;
         __syncthreads();
+    }
+}
+
+// ----------------------------------------------- warp-pipelined SpMV
+// Each warp owns `ns` shared-memory stages with their own mbarriers and
+// streams its own tiles (at most 32 / V rows and `capw` entries): lane 0
+// issues the bulk copies of the tile ns - 1 ahead, the warp waits on its
+// stage, sums its rows, and only synchronises with itself before the stage is
+// reused.  No CTA-wide barrier: a warp whose gathers hit is not held back by
+// one whose gathers miss.
+constexpr int WPB = NT / 32;  // warps per CTA
+
+__host__ __device__ __forceinline__ int warp_smem_bytes(int capw, int rowsw, int ns)
+{
+    return 16 * kMaxStages * WPB + WPB * ns * stage_layout(capw, rowsw).bytes;
+}
+
+template <int V, bool F32, int MODE>
+__global__ void __launch_bounds__(NT)
+    k_spmv_w(Csr3 A, const double *x, const double *bll, const double *bnl, double *y, Scale sc,
+             const Item *tiles, int n_tiles, int capw, int rowsw, int ns, int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (*(volatile const int *)err) return;  // sticky error: no work until cleared
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const StageLayout L = stage_layout(capw, rowsw);
+    unsigned char *mine = smem + 16 * kMaxStages * WPB + warp * ns * L.bytes;
+    auto stage = [&](int s2) {
+        TileStage t;
+        t.bar = reinterpret_cast<uint64_t *>(smem + 16 * (warp * kMaxStages + s2));
+        unsigned char *p = mine + s2 * L.bytes;
+        t.rows = reinterpret_cast<int *>(p + L.rows);
+        t.col = reinterpret_cast<uint32_t *>(p + L.col);
+        t.val = reinterpret_cast<double *>(p + L.val);
+        return t;
+    };
+    if (lane == 0) {
+        for (int s2 = 0; s2 < ns; s2++) mbar_init(stage(s2).bar, 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    // a contiguous block of tiles per CTA, its warps interleaved inside it
+    const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+    const int q0 = blockIdx.x * per, q1 = min(n_tiles, q0 + per);
+    if (lane == 0)
+        for (int i = 0; i < ns - 1; i++) {
+            const int q = q0 + warp + i * WPB;
+            if (q >= q1) break;
+            const Item it = tiles[q];
+            if (staged_tile(it, capw)) tile_issue<F32>(A, stage(i), it.b, it.e, it.k0, it.k1);
+        }
+    uint32_t phase = 0;
+    int cur = 0;
+    for (int q = q0 + warp; q < q1; q += WPB) {
+        const Item it = tiles[q];
+        const int qa = q + (ns - 1) * WPB;
+        if (lane == 0 && qa < q1) {
+            const Item ita = tiles[qa];
+            if (staged_tile(ita, capw))
+                tile_issue<F32>(A, stage((cur + ns - 1) % ns), ita.b, ita.e, ita.k0, ita.k1);
+        }
+        const int nr = it.e - it.b;
+        if (staged_tile(it, capw)) {
+            const TileStage st = stage(cur);
+            const bool ok = tile_wait(st, (phase >> cur) & 1, err);
+            phase ^= 1u << cur;
+            if (ok) {
+                const int rb = it.b & ~3, kb = it.k0 & ~3;
+                const int sub = lane & (V - 1), grp = lane / V;
+                const float *val32 = reinterpret_cast<const float *>(st.val);
+                for (int base = 0; base < nr; base += 32 / V) {
+                    const int i = base + grp;
+                    double acc = 0.0;
+                    if (MODE == kRemote && i < nr && sub == 0) acc = y[it.b + i];
+                    if (i < nr) {
+                        const int s0 = st.rows[it.b - rb + i] - kb, e0 = st.rows[it.b - rb + i + 1] - kb;
+#pragma unroll 8
+                        for (int k = s0 + sub; k < e0; k += V) {
+                            const double xv = load_x<false>(st.col[k], x, bll, bnl);
+                            if (F32)
+                                acc = __dadd_rn(acc, (double)__fmul_rn(val32[k], __double2float_rn(xv)));
+                            else
+                                acc = fma(st.val[k], xv, acc);
+                        }
+                    }
+                    if (V > 1) {
+#pragma unroll
+                        for (int o = V / 2; o > 0; o >>= 1)
+                            acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+                    }
+                    if (i < nr && sub == 0) y[it.b + i] = MODE == kLocal ? acc : apply_scale(acc, sc);
+                }
+            }
+        } else {
+            // a row longer than a warp stage: the warp sums it from global memory
+            for (int r = it.b; r < it.e; r++) {
+                const int s0 = ld_stream_s32(A.rowptr + r), e0 = ld_stream_s32(A.rowptr + r + 1);
+                double acc = 0.0;
+                for (int k = s0 + lane; k < e0; k += 32) {
+                    const double xv = load_x<false>(ld_stream_u32(A.colenc + k), x, bll, bnl);
+                    if (F32)
+                        acc = __dadd_rn(acc, (double)__fmul_rn(ld_stream_f32(A.val32 + k),
+                                                               __double2float_rn(xv)));
+                    else
+                        acc = fma(ld_stream_f64(A.val + k), xv, acc);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+                if (lane == 0) {
+                    if (MODE == kRemote) acc = __dadd_rn(y[r], acc);
+                    y[r] = MODE == kLocal ? acc : apply_scale(acc, sc);
+                }
+            }
+        }
+        cur = cur + 1 == ns ? 0 : cur + 1;
+        __syncwarp();
     }
 }
 
@@ -843,6 +961,7 @@ napspmv_opts resolve_opts(const napspmv_plan_t *P, const napspmv_opts *o)
     if (o->tile_rows) r.tile_rows = o->tile_rows;
     if (o->tile_nnz) r.tile_nnz = o->tile_nnz;
     if (o->stages) r.stages = o->stages;
+    if (o->pipeline) r.pipeline = o->pipeline;
     if (o->timeout_ms) r.timeout_ms = o->timeout_ms;
     r.debug_stall = o->debug_stall;
     return r;
@@ -936,6 +1055,32 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
         cut(P->h_rowptrL, tl);
         cut(P->h_rowptrR, tr);
     }
+    // warp tiles: the same cutting with a warp's share of a CTA tile
+    std::vector<Item> wt, wtl, wtr;
+    {
+        const int32_t trows = tile_rows, tnnz = tile_nnz;
+        tile_rows = std::max(1, trows / 8);
+        tile_nnz = std::max(32, tnnz / 8);
+        cut(P->h_rowptr, wt);
+        if (!P->h_rowptrL.empty()) {
+            cut(P->h_rowptrL, wtl);
+            cut(P->h_rowptrR, wtr);
+        }
+        tile_rows = trows;
+        tile_nnz = tnnz;
+    }
+    auto upload_items = [&](const std::vector<Item> &v, Item **d, int32_t *n) -> int {
+        if (*d) cudaFree(*d);
+        *d = nullptr;
+        *n = (int32_t)v.size();
+        if (v.empty()) return NAPSPMV_OK;
+        NAP_CUDA(cudaMalloc(d, sizeof(Item) * v.size()));
+        NAP_CUDA(cudaMemcpy(*d, v.data(), sizeof(Item) * v.size(), cudaMemcpyHostToDevice));
+        return NAPSPMV_OK;
+    };
+    if (int rc = upload_items(wt, &S.d_wt, &S.n_wt)) return rc;
+    if (int rc = upload_items(wtl, &S.d_wtL, &S.n_wtL)) return rc;
+    if (int rc = upload_items(wtr, &S.d_wtR, &S.n_wtR)) return rc;
     Item *d_tl = nullptr, *d_tr = nullptr;
     if (!tl.empty()) {
         NAP_CUDA(cudaMalloc(&d_tl, sizeof(Item) * tl.size()));
@@ -1091,8 +1236,16 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
 using SpmvKernel = void (*)(Csr3, const double *, const double *, const double *, double *, Scale,
                             const Item *, int, int, int, int, int *);
 template <bool F32, int MODE>
-static SpmvKernel pick_spmv(int vec)
+static SpmvKernel pick_spmv(int vec, bool warp = false)
 {
+    if (warp) switch (vec) {
+        case 1: return k_spmv_w<1, F32, MODE>;
+        case 2: return k_spmv_w<2, F32, MODE>;
+        case 4: return k_spmv_w<4, F32, MODE>;
+        case 8: return k_spmv_w<8, F32, MODE>;
+        case 16: return k_spmv_w<16, F32, MODE>;
+        default: return k_spmv_w<32, F32, MODE>;
+        }
     switch (vec) {
     case 1: return k_spmv<1, F32, MODE>;
     case 2: return k_spmv<2, F32, MODE>;
@@ -1103,47 +1256,71 @@ static SpmvKernel pick_spmv(int vec)
     }
 }
 
+// Kernel, tiles, capacities, shared memory and grid of one SpMV launch
+// (mode: full three-block pass, local part, remote part).
+struct SpmvLaunch {
+    SpmvKernel fn = nullptr;
+    Csr3 A{};
+    const Item *tiles = nullptr;
+    int n = 0, cap = 0, rows = 0, grid = 1;
+    size_t sm = 0;
+};
+static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode, SpmvLaunch &L)
+{
+    const bool f32 = o.precision == NAPSPMV_PREC_F32;
+    const bool warp = o.pipeline == NAPSPMV_PIPELINE_WARP;
+    const ItemSet &S = P->items;
+    L.cap = warp ? std::max(32, o.tile_nnz / WPB) : o.tile_nnz;
+    L.rows = warp ? std::max(1, o.tile_rows / WPB) : o.tile_rows;
+    L.sm = warp ? (size_t)warp_smem_bytes(L.cap, L.rows, o.stages)
+                : smem_bytes(o.tile_nnz, o.tile_rows, o.stages);
+    if (mode == kLocal) {
+        L.A = Csr3{P->d_rowptrL, P->d_colL, P->d_valL, f32 ? P->d_val32L : nullptr};
+        L.fn = f32 ? pick_spmv<true, kLocal>(o.vec, warp) : pick_spmv<false, kLocal>(o.vec, warp);
+        L.tiles = warp ? S.d_wtL : S.d_tilesL;
+        L.n = warp ? S.n_wtL : S.n_tilesL;
+    } else if (mode == kRemote) {
+        L.A = Csr3{P->d_rowptrR, P->d_colR, P->d_valR, f32 ? P->d_val32R : nullptr};
+        L.fn = f32 ? pick_spmv<true, kRemote>(o.vec, warp) : pick_spmv<false, kRemote>(o.vec, warp);
+        L.tiles = warp ? S.d_wtR : S.d_tilesR;
+        L.n = warp ? S.n_wtR : S.n_tilesR;
+    } else {
+        L.A = Csr3{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
+        L.fn = f32 ? pick_spmv<true, kFull>(o.vec, warp) : pick_spmv<false, kFull>(o.vec, warp);
+        L.tiles = warp ? S.d_wt : S.d_items + S.spmv_first;
+        L.n = warp ? S.n_wt : S.n_items - S.spmv_first;
+    }
+    if (int rc = prepare_smem(L.fn, L.sm)) return rc;
+    int occ = 0;
+    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, NT, L.sm));
+    const int ctas = warp ? (L.n + WPB - 1) / WPB : L.n;
+    L.grid = std::max(1, std::min(ctas, P->num_sms * std::max(occ, 1)));
+    if (mode == kLocal)  // leave one CTA slot per SM for the message steps
+        L.grid = std::max(1, std::min(ctas, P->num_sms * std::max(occ - 1, 1)));
+    return NAPSPMV_OK;
+}
+static void spmv_run(const SpmvLaunch &L, const double *x, const napspmv_ws_t *ws, double *y,
+                     double scale, int stages, cudaStream_t s)
+{
+    L.fn<<<L.grid, NT, L.sm, s>>>(L.A, x, ws->bll, ws->bnl, y, make_scale(scale), L.tiles, L.n,
+                                  L.cap, L.rows, stages, ws->err);
+}
+
 static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
                           double scale, const napspmv_opts &o, cudaStream_t s, int64_t *kernels)
 {
-    const bool f32 = o.precision == NAPSPMV_PREC_F32;
     auto grid = [&](int64_t n) {
         return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
                                                             (int64_t)P->num_sms * 8));
     };
-    Csr3 A{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
-    using SpmvFn = void (*)(Csr3, const double *, const double *, const double *, double *, Scale,
-                            const Item *, int, int, int, int, int *);
-    SpmvFn sp = nullptr;
-#define NAP_CASE(V) \
-    case V: sp = f32 ? k_spmv<V, true> : k_spmv<V, false>; break;
-    switch (o.vec) {
-        NAP_CASE(1)
-        NAP_CASE(2)
-        NAP_CASE(4)
-        NAP_CASE(8)
-        NAP_CASE(16)
-        NAP_CASE(32)
-    }
-#undef NAP_CASE
-    const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows, o.stages);
     const ItemSet &S = P->items;
-    const int n_tiles = S.n_items - S.spmv_first;
-    int occ = 0;
-    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sp, NT, sm));
-    const int sp_grid = std::max(1, std::min(n_tiles, P->num_sms * std::max(occ, 1)));
     const bool overlap = o.engine == NAPSPMV_ENGINE_OVERLAP && S.n_tilesL > 0;
-    Csr3 AL{P->d_rowptrL, P->d_colL, P->d_valL, f32 ? P->d_val32L : nullptr};
-    Csr3 AR{P->d_rowptrR, P->d_colR, P->d_valR, f32 ? P->d_val32R : nullptr};
-    SpmvFn spL = f32 ? pick_spmv<true, kLocal>(o.vec) : pick_spmv<false, kLocal>(o.vec);
-    SpmvFn spR = f32 ? pick_spmv<true, kRemote>(o.vec) : pick_spmv<false, kRemote>(o.vec);
+    SpmvLaunch LF, LL, LR;
+    if (int rc = spmv_launch(P, o, kFull, LF)) return rc;
     if (overlap) {
-        if (int rc = prepare_smem(spL, sm)) return rc;
-        if (int rc = prepare_smem(spR, sm)) return rc;
+        if (int rc = spmv_launch(P, o, kLocal, LL)) return rc;
+        if (int rc = spmv_launch(P, o, kRemote, LR)) return rc;
     }
-    // the local part leaves one CTA slot per SM free for the message steps
-    const int gridL = std::max(1, std::min(S.n_tilesL, P->num_sms * std::max(occ - 1, 1)));
-    const int gridR = std::max(1, std::min(S.n_tilesR, P->num_sms * std::max(occ, 1)));
     int64_t nk = 0;
     for (int k = 0; k < reps; k++) {
         const double *x = (k == 0) ? v : (((reps - k) & 1) == 0 ? w : ws->xtmp);
@@ -1153,9 +1330,7 @@ static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, 
             // runs on a second stream while the message steps proceed
             NAP_CUDA(cudaEventRecord(P->ev_fork, s));
             NAP_CUDA(cudaStreamWaitEvent(P->aux, P->ev_fork, 0));
-            spL<<<gridL, NT, sm, P->aux>>>(AL, x, ws->bll, ws->bnl, y, make_scale(scale),
-                                             S.d_tilesL, S.n_tilesL, o.tile_nnz, o.tile_rows,
-                                             o.stages, ws->err);
+            spmv_run(LL, x, ws, y, scale, o.stages, P->aux);
             nk++;
             NAP_CUDA(cudaEventRecord(P->ev_join, P->aux));
         }
@@ -1179,12 +1354,9 @@ static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, 
         }
         if (overlap) {
             NAP_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
-            spR<<<gridR, NT, sm, s>>>(AR, x, ws->bll, ws->bnl, y, make_scale(scale), S.d_tilesR,
-                                      S.n_tilesR, o.tile_nnz, o.tile_rows, o.stages, ws->err);
+            spmv_run(LR, x, ws, y, scale, o.stages, s);
         } else {
-            sp<<<sp_grid, NT, sm, s>>>(A, x, ws->bll, ws->bnl, y, make_scale(scale),
-                                       S.d_items + S.spmv_first, n_tiles, o.tile_nnz,
-                                       o.tile_rows, o.stages, ws->err);
+            spmv_run(LF, x, ws, y, scale, o.stages, s);
         }
         nk++;
         NAP_CUDA(cudaGetLastError());
@@ -1199,22 +1371,13 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
                          double scale, const napspmv_opts &o, cudaStream_t s)
 {
     {
-        const bool f32 = o.precision == NAPSPMV_PREC_F32;
-        const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows, o.stages);
-        int rc = NAPSPMV_OK;
-#define NAP_CASE(V)                                                                  \
-    case V: rc = f32 ? prepare_smem(k_spmv<V, true>, sm) : prepare_smem(k_spmv<V, false>, sm); \
-        break;
-        switch (o.vec) {
-            NAP_CASE(1)
-            NAP_CASE(2)
-            NAP_CASE(4)
-            NAP_CASE(8)
-            NAP_CASE(16)
-            NAP_CASE(32)
+        // attributes (dynamic shared memory) are set before any capture
+        SpmvLaunch L;
+        if (int rc = spmv_launch(P, o, kFull, L)) return rc;
+        if (o.engine == NAPSPMV_ENGINE_OVERLAP && P->items.n_tilesL > 0) {
+            if (int rc = spmv_launch(P, o, kLocal, L)) return rc;
+            if (int rc = spmv_launch(P, o, kRemote, L)) return rc;
         }
-#undef NAP_CASE
-        if (rc) return rc;
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     NAP_CUDA(cudaStreamIsCapturing(s, &cs));
@@ -1229,7 +1392,8 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
         auto &g = P->graphs[i];
         if (g.v == v && g.w == w && g.ws == ws && g.reps == reps && g.scale == scale &&
             g.prec == o.precision && g.vec == o.vec && g.tile_rows == o.tile_rows &&
-            g.tile_nnz == o.tile_nnz) {
+            g.tile_nnz == o.tile_nnz && g.engine == o.engine && g.stages == o.stages &&
+            g.pipeline == o.pipeline) {
             NAP_CUDA(cudaGraphLaunch(g.exec, s));
             count_launch(g.kernels);
             return NAPSPMV_OK;
@@ -1252,7 +1416,8 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
         cudaGraphExecDestroy(P->graphs.front().exec);
         P->graphs.erase(P->graphs.begin());
     }
-    P->graphs.push_back({v, w, ws, reps, o.precision, o.vec, o.tile_rows, o.tile_nnz, scale, exec, nk});
+    P->graphs.push_back({v, w, ws, reps, o.precision, o.vec, o.tile_rows, o.tile_nnz, o.engine,
+                         o.stages, o.pipeline, scale, exec, nk});
     NAP_CUDA(cudaGraphLaunch(exec, s));
     count_launch(nk);
     return NAPSPMV_OK;
@@ -1279,6 +1444,10 @@ static int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
     }
     if (o.timeout_ms < 1) {
         set_error(NAPSPMV_ERR_ARG, "timeout_ms must be >= 1");
+        return NAPSPMV_ERR_ARG;
+    }
+    if (o.pipeline != NAPSPMV_PIPELINE_CTA && o.pipeline != NAPSPMV_PIPELINE_WARP) {
+        set_error(NAPSPMV_ERR_ARG, "pipeline must be NAPSPMV_PIPELINE_CTA or _WARP");
         return NAPSPMV_ERR_ARG;
     }
     if (o.stages < 2 || o.stages > kMaxStages ||
@@ -1471,32 +1640,9 @@ extern "C" int napspmv_spmv_step(napspmv_plan_t *P, napspmv_ws_t *ws, const doub
     NAP_CUDA(cudaGetDevice(&cur));
     if (cur != P->device) NAP_CUDA(cudaSetDevice(P->device));
     if ((rc = build_items(P, o.chunk, o.tile_rows, o.tile_nnz))) return rc;
-    const bool f32 = o.precision == NAPSPMV_PREC_F32;
-    Csr3 A{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
-    using SpmvFn = void (*)(Csr3, const double *, const double *, const double *, double *, Scale,
-                            const Item *, int, int, int, int, int *);
-    SpmvFn sp = nullptr;
-#define NAP_CASE(V) \
-    case V: sp = f32 ? k_spmv<V, true> : k_spmv<V, false>; break;
-    switch (o.vec) {
-        NAP_CASE(1)
-        NAP_CASE(2)
-        NAP_CASE(4)
-        NAP_CASE(8)
-        NAP_CASE(16)
-        NAP_CASE(32)
-    }
-#undef NAP_CASE
-    const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows, o.stages);
-    if ((rc = prepare_smem(sp, sm))) return rc;
-    const ItemSet &S = P->items;
-    const int n_tiles = S.n_items - S.spmv_first;
-    int occ = 0;
-    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sp, NT, sm));
-    sp<<<std::max(1, std::min(n_tiles, P->num_sms * std::max(occ, 1))), NT, sm,
-         (cudaStream_t)stream>>>(A, v, W->bll, W->bnl, w, make_scale(scale),
-                                 S.d_items + S.spmv_first, n_tiles, o.tile_nnz, o.tile_rows,
-                                 o.stages, W->err);
+    SpmvLaunch L;
+    if ((rc = spmv_launch(P, o, kFull, L))) return rc;
+    spmv_run(L, v, W, w, scale, o.stages, (cudaStream_t)stream);
     count_launch(1);
     NAP_CUDA(cudaGetLastError());
     if (cur != P->device) cudaSetDevice(cur);

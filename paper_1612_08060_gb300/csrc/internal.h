@@ -64,6 +64,10 @@ struct ItemSet {
     int32_t spmv_first = 0;  // items [spmv_first, n_items) are the row tiles
     Item *d_tilesL = nullptr, *d_tilesR = nullptr;  // tiles of the split parts
     int32_t n_tilesL = 0, n_tilesR = 0;
+    // warp tiles (at most tile_rows / 8 rows, tile_nnz / 8 entries) of the whole
+    // matrix and of its two split parts
+    Item *d_wt = nullptr, *d_wtL = nullptr, *d_wtR = nullptr;
+    int32_t n_wt = 0, n_wtL = 0, n_wtR = 0;
     Item *d_items = nullptr;
     // per-apply increments of every counter, [kNumCounters][nn]
     uint64_t *d_cnt = nullptr;
@@ -140,7 +144,7 @@ struct napspmv_plan_s {
     // instantiated CUDA graphs of chained phased applies, newest last
     struct GraphEntry {
         const void *v, *w, *ws;
-        int32_t reps, prec, vec, tile_rows, tile_nnz;
+        int32_t reps, prec, vec, tile_rows, tile_nnz, engine, stages, pipeline;
         double scale;
         cudaGraphExec_t exec;
         int64_t kernels;

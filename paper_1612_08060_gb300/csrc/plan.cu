@@ -961,6 +961,7 @@ void plan_free(napspmv_plan_t *P)
     void *ptrs[] = {P->d_split, P->d_rowptr, P->d_colenc, P->d_val, P->d_val32, P->d_pack_src,
                     P->d_xfer_dst, P->d_unp_src, P->d_gs_msg_off, P->d_gs_msg_dstnode,
                     P->items.d_items, P->items.d_cnt, P->items.d_tilesL, P->items.d_tilesR,
+                    P->items.d_wt, P->items.d_wtL, P->items.d_wtR,
                     P->d_rowptrL, P->d_rowptrR, P->d_colL, P->d_colR, P->d_valL, P->d_valR,
                     P->d_val32L, P->d_val32R};
     if (P->aux) cudaStreamDestroy(P->aux);
@@ -1017,6 +1018,11 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         int vec = avg <= 16 ? 1 : avg <= 32 ? 2 : avg <= 96 ? 4 : avg <= 384 ? 16 : 32;
         int rows = 512 / vec;
         int cap = 2048;
+        // several lanes per row: tiles bounded by entries, not rows, and warp
+        // tiles (measured on the 2^23-row banded random workload, about 20
+        // entries per row: 1024-row / 2048-entry CTA tiles split over the
+        // warps beat smaller tiles and the CTA pipeline)
+        if (vec > 1) rows = 1024;
         P->defaults.precision = NAPSPMV_PREC_F64;
         P->defaults.engine = NAPSPMV_ENGINE_OVERLAP;
         P->defaults.vec = vec;
@@ -1025,6 +1031,7 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         P->defaults.tile_rows = rows;
         P->defaults.tile_nnz = cap;
         P->defaults.stages = 2;
+        P->defaults.pipeline = vec > 1 ? NAPSPMV_PIPELINE_WARP : NAPSPMV_PIPELINE_CTA;
         P->defaults.timeout_ms = 10000;
         P->defaults.debug_stall = 0;
         rc = build_items(P, P->defaults.chunk, P->defaults.tile_rows, P->defaults.tile_nnz);

@@ -25,7 +25,9 @@ def run(plan, v, reps=1, scale=1.0, **opts):
 
 
 ENGINES = [dict(engine=nap.ENGINE_FUSED), dict(engine=nap.ENGINE_PHASED),
-           dict(engine=nap.ENGINE_OVERLAP)]
+           dict(engine=nap.ENGINE_OVERLAP),
+           dict(engine=nap.ENGINE_PHASED, pipeline=nap.PIPELINE_WARP),
+           dict(engine=nap.ENGINE_OVERLAP, pipeline=nap.PIPELINE_WARP)]
 SHAPES = [dict(vec=v) for v in (1, 2, 4, 8, 32)]
 
 
