@@ -109,7 +109,9 @@ typedef struct {
     int32_t precision;   /* NAPSPMV_PREC_F64 or NAPSPMV_PREC_F32               */
     int32_t engine;      /* NAPSPMV_ENGINE_DEFAULT, _FUSED, _PHASED, _OVERLAP  */
     int32_t vec;         /* lanes per matrix row: 1, 2, 4, 8, 16 or 32         */
-    int32_t ctas_per_sm; /* persistent CTAs per SM (fused engine)              */
+    int32_t ctas_per_sm; /* resident CTAs per SM: the persistent CTAs of the
+                            fused engine; a cap on the SpMV grid of the
+                            phased / overlapped engines                       */
     int32_t chunk;       /* gather elements per work item (fused engine)       */
     int32_t tile_rows;   /* at most this many matrix rows per SpMV work item   */
     int32_t tile_nnz;    /* at most this many stored entries per SpMV work item

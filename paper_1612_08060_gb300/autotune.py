@@ -2,15 +2,15 @@
 
 Searches the engine (overlapped, phased, fused), lanes per row (``vec``), the
 SpMV tile shape (``tile_rows``, ``tile_nnz``: the entries one shared-memory
-stage holds), the pipeline depth (``stages``), CTA or warp tiles (``pipeline``)
+stage holds), the pipeline depth (``stages``), CTA or warp tiles
+(``pipeline``), resident CTAs per SM (``ctas_per_sm``, 0 = occupancy maximum)
 and the gather chunk of the fused engine's message items (``chunk``) by
-coordinate descent: starting from the
-plan's defaults, each parameter in turn is set to each candidate while the
-others stay fixed, the fastest is kept, and the sweep repeats until nothing
-improves.  Each candidate is timed with CUDA events over chained applies
-(inputs already on the device).  The winner is installed with
-napspmv_set_default_opts and cached per (N, nnz, nnz-per-row histogram, n_p,
-ppn, precision) key, in memory and optionally in a JSON file.
+coordinate descent: starting from the plan's defaults, each parameter in turn
+is set to each candidate while the others stay fixed, the fastest is kept, and
+the sweep repeats until nothing improves.  Each candidate is timed with CUDA
+events over chained applies (inputs already on the device).  The winner is
+installed with napspmv_set_default_opts and cached per (N, nnz, nnz-per-row
+histogram, n_p, ppn, precision) key, in memory and optionally in a JSON file.
 """
 from __future__ import annotations
 
@@ -28,6 +28,7 @@ CANDIDATES = {
     "tile_rows": [256, 384, 512, 1024],
     "stages": [2, 3],
     "pipeline": [nap.PIPELINE_CTA, nap.PIPELINE_WARP],
+    "ctas_per_sm": [0, 2, 3, 4],
     "chunk": [2048, 4096, 8192],
 }
 

@@ -1069,6 +1069,27 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
         tile_rows = trows;
         tile_nnz = tnnz;
     }
+    // the stage each list needs: its largest tile that is staged at all
+    auto fit = [](const std::vector<Item> &v, int32_t tnnz, int32_t &cap, int32_t &rows) {
+        cap = 32;
+        rows = 1;
+        for (const Item &it : v)
+            if (it.kind == kSpmv && it.k1 - it.k0 <= tnnz) {
+                cap = std::max(cap, it.k1 - it.k0);
+                rows = std::max(rows, it.e - it.b);
+            }
+        cap = std::min(tnnz, (cap + 15) & ~15);
+    };
+    {
+        const std::vector<Item> whole(items.begin() + spmv_first, items.end());
+        const int32_t wn = std::max(32, tile_nnz / 8);
+        fit(whole, tile_nnz, S.fit_nnz[0], S.fit_rows[0]);
+        fit(tl, tile_nnz, S.fit_nnz[1], S.fit_rows[1]);
+        fit(tr, tile_nnz, S.fit_nnz[2], S.fit_rows[2]);
+        fit(wt, wn, S.fit_nnz[3], S.fit_rows[3]);
+        fit(wtl, wn, S.fit_nnz[4], S.fit_rows[4]);
+        fit(wtr, wn, S.fit_nnz[5], S.fit_rows[5]);
+    }
     auto upload_items = [&](const std::vector<Item> &v, Item **d, int32_t *n) -> int {
         if (*d) cudaFree(*d);
         *d = nullptr;
@@ -1270,10 +1291,11 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
     const bool warp = o.pipeline == NAPSPMV_PIPELINE_WARP;
     const ItemSet &S = P->items;
-    L.cap = warp ? std::max(32, o.tile_nnz / WPB) : o.tile_nnz;
-    L.rows = warp ? std::max(1, o.tile_rows / WPB) : o.tile_rows;
+    const int list = (warp ? 3 : 0) + (mode == kLocal ? 1 : mode == kRemote ? 2 : 0);
+    L.cap = S.fit_nnz[list];
+    L.rows = S.fit_rows[list];
     L.sm = warp ? (size_t)warp_smem_bytes(L.cap, L.rows, o.stages)
-                : smem_bytes(o.tile_nnz, o.tile_rows, o.stages);
+                : smem_bytes(L.cap, L.rows, o.stages);
     if (mode == kLocal) {
         L.A = Csr3{P->d_rowptrL, P->d_colL, P->d_valL, f32 ? P->d_val32L : nullptr};
         L.fn = f32 ? pick_spmv<true, kLocal>(o.vec, warp) : pick_spmv<false, kLocal>(o.vec, warp);
@@ -1292,7 +1314,24 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
     }
     if (int rc = prepare_smem(L.fn, L.sm)) return rc;
     int occ = 0;
+    NAP_CUDA(cudaFuncSetAttribute(L.fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared));
     NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, NT, L.sm));
+    // resident CTAs per SM: the occupancy maximum, or fewer (ctas_per_sm) where
+    // the gathers want L1 more than the extra warps
+    if (o.ctas_per_sm > 0) occ = std::min(occ, o.ctas_per_sm);
+    // shared-memory carveout: what those CTAs need, the rest of the SM's unified
+    // L1 / shared storage stays L1 for the gathers
+    {
+        int smem_sm = 0, reserved = 0;
+        NAP_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                        P->device));
+        NAP_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock,
+                                        P->device));
+        const int64_t need = (int64_t)std::max(occ, 1) * ((int64_t)L.sm + reserved);
+        const int pct = (int)std::min<int64_t>(100, (need * 100 + smem_sm - 1) / smem_sm);
+        NAP_CUDA(cudaFuncSetAttribute(L.fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    }
     const int ctas = warp ? (L.n + WPB - 1) / WPB : L.n;
     L.grid = std::max(1, std::min(ctas, P->num_sms * std::max(occ, 1)));
     if (mode == kLocal)  // leave one CTA slot per SM for the message steps
@@ -1393,7 +1432,7 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
         if (g.v == v && g.w == w && g.ws == ws && g.reps == reps && g.scale == scale &&
             g.prec == o.precision && g.vec == o.vec && g.tile_rows == o.tile_rows &&
             g.tile_nnz == o.tile_nnz && g.engine == o.engine && g.stages == o.stages &&
-            g.pipeline == o.pipeline) {
+            g.pipeline == o.pipeline && g.ctas_per_sm == o.ctas_per_sm) {
             NAP_CUDA(cudaGraphLaunch(g.exec, s));
             count_launch(g.kernels);
             return NAPSPMV_OK;
@@ -1417,7 +1456,7 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
         P->graphs.erase(P->graphs.begin());
     }
     P->graphs.push_back({v, w, ws, reps, o.precision, o.vec, o.tile_rows, o.tile_nnz, o.engine,
-                         o.stages, o.pipeline, scale, exec, nk});
+                         o.stages, o.pipeline, o.ctas_per_sm, scale, exec, nk});
     NAP_CUDA(cudaGraphLaunch(exec, s));
     count_launch(nk);
     return NAPSPMV_OK;

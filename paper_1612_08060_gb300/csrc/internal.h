@@ -68,6 +68,10 @@ struct ItemSet {
     // matrix and of its two split parts
     Item *d_wt = nullptr, *d_wtL = nullptr, *d_wtR = nullptr;
     int32_t n_wt = 0, n_wtL = 0, n_wtR = 0;
+    // largest staged tile (entries, rows) of each list, in the order whole /
+    // local / remote CTA tiles, then whole / local / remote warp tiles: a
+    // stage is sized to what its list needs, not to tile_nnz
+    int32_t fit_nnz[6] = {}, fit_rows[6] = {};
     Item *d_items = nullptr;
     // per-apply increments of every counter, [kNumCounters][nn]
     uint64_t *d_cnt = nullptr;
@@ -144,7 +148,7 @@ struct napspmv_plan_s {
     // instantiated CUDA graphs of chained phased applies, newest last
     struct GraphEntry {
         const void *v, *w, *ws;
-        int32_t reps, prec, vec, tile_rows, tile_nnz, engine, stages, pipeline;
+        int32_t reps, prec, vec, tile_rows, tile_nnz, engine, stages, pipeline, ctas_per_sm;
         double scale;
         cudaGraphExec_t exec;
         int64_t kernels;

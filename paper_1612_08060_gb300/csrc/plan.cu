@@ -1013,25 +1013,33 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         double avg = (double)P->nnz / (double)P->n;
         // rows are summed from shared memory; one lane per row keeps exactly one
         // FP64 FMA per stored entry (GB300's FP64 pipe is the scarce unit).
-        // (measured on the 128^3 7-point workload: two stages of 2048 entries
-        // beat deeper pipelines, which cost CTAs per SM)
+        // (measured: two stages of 1536 entries beat 2048 on the 2^21-row 7-point
+        // and the 2^22-row 9-point workloads, and deeper pipelines, which cost
+        // CTAs per SM)
         int vec = avg <= 16 ? 1 : avg <= 32 ? 2 : avg <= 96 ? 4 : avg <= 384 ? 16 : 32;
         int rows = 512 / vec;
-        int cap = 2048;
-        // several lanes per row: tiles bounded by entries, not rows, and warp
-        // tiles (measured on the 2^23-row banded random workload, about 20
-        // entries per row: 1024-row / 2048-entry CTA tiles split over the
-        // warps beat smaller tiles and the CTA pipeline)
-        if (vec > 1) rows = 1024;
+        int cap = 1536;
+        int ctas = 0;  // occupancy maximum
+        int pipeline = NAPSPMV_PIPELINE_CTA;
+        // several lanes per row: the gathers dominate and want L1.  Measured on
+        // the 2^23-row banded random workload (about 20 entries per row):
+        // 1024-row / 2048-entry CTA tiles split into warp tiles, three CTAs per
+        // SM (the fourth CTA's shared memory leaves the gathers too little L1)
+        if (vec > 1) {
+            rows = 1024;
+            cap = 2048;
+            ctas = 3;
+            pipeline = NAPSPMV_PIPELINE_WARP;
+        }
         P->defaults.precision = NAPSPMV_PREC_F64;
         P->defaults.engine = NAPSPMV_ENGINE_OVERLAP;
         P->defaults.vec = vec;
-        P->defaults.ctas_per_sm = 0;  // occupancy maximum
+        P->defaults.ctas_per_sm = ctas;
         P->defaults.chunk = 4096;
         P->defaults.tile_rows = rows;
         P->defaults.tile_nnz = cap;
         P->defaults.stages = 2;
-        P->defaults.pipeline = vec > 1 ? NAPSPMV_PIPELINE_WARP : NAPSPMV_PIPELINE_CTA;
+        P->defaults.pipeline = pipeline;
         P->defaults.timeout_ms = 10000;
         P->defaults.debug_stall = 0;
         rc = build_items(P, P->defaults.chunk, P->defaults.tile_rows, P->defaults.tile_nnz);
