@@ -264,11 +264,23 @@ def main():
     f32 = args.precision == "f32"
     B = bytes_per_apply(A, st) - (4.0 * A.nnz if f32 else 0.0)
     B_csr = st["bytes_csr_f32"] if f32 else st["bytes_csr_f64"]
-    # SpMV step alone: row pointer, column + value streams, each x and each
-    # received value read once, w written once
-    B_spmv = 4.0 * (A.n + 1) + (8.0 if f32 else 12.0) * A.nnz + 16.0 * A.n + 8.0 * (
-        st["bll_total"] + st["bnl_total"])
     assert abs(B - (B_csr + st["bytes_msg"])) < 1.0
+    # FP32 mode of the phased / overlapped engines moves FP32 copies through the
+    # message steps: 4 B read + 4 B write + 4 B index per element and hop
+    # instead of 8 + 8 + 4 (the fused engine keeps FP64 messages)
+    f32_msgs = f32 and args.engine != "fused"
+    if f32_msgs:
+        B -= st["bytes_msg"] * 8.0 / 20.0
+    # SpMV step alone: row pointer, column + value streams, each x and each
+    # received value read once, w written once; in FP32 mode the step also
+    # makes the FP32 copy of x (8 B read + 4 B written per row) and reads
+    # 4-byte copies
+    if f32:
+        B_spmv = 4.0 * (A.n + 1) + 8.0 * A.nnz + 24.0 * A.n + 4.0 * (
+            st["bll_total"] + st["bnl_total"])
+    else:
+        B_spmv = 4.0 * (A.n + 1) + 12.0 * A.nnz + 16.0 * A.n + 8.0 * (
+            st["bll_total"] + st["bnl_total"])
     opts = nap.make_opts(engine={"default": nap.ENGINE_DEFAULT, "fused": nap.ENGINE_FUSED,
                                  "phased": nap.ENGINE_PHASED,
                                  "overlap": nap.ENGINE_OVERLAP}[args.engine],
@@ -324,8 +336,13 @@ def main():
         rc = nap.napspmv_status(plan, stream)
         assert rc == 0, rc
     # the dominant kernel (three-block SpMV, a11) timed alone on the same stream
+    # (FP32: after a phased apply, whose receive buffers hold the FP32 copies)
     with torch.cuda.stream(stream):
-        nap.napspmv_apply_ex(plan, vd, wd, 1, 1.0, opts, stream=stream)
+        ro = opts
+        if f32:
+            ro = nap.make_opts(**{k: getattr(opts, k) for k, _ in opts._fields_})
+            ro.engine = nap.ENGINE_PHASED
+        nap.napspmv_apply_ex(plan, vd, wd, 1, 1.0, ro, stream=stream)
         sp_n = 50
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -383,7 +400,7 @@ def main():
                    "l2": "inputs larger than L2: each apply streams the 175 MB col/val "
                          "arrays (L2 129 MB); not flushed between steps",
                    "parallelism": f"replicas{ws}"},
-        "bytes_per_apply": {"total": B, "csr": B_csr, "msg": st["bytes_msg"]},
+        "bytes_per_apply": {"total": B, "csr": B_csr, "msg": B - B_csr},
         "csr_gbs": round(B_csr * args.reps / (avg_launch * 1e-3) / 1e9, 3),
         "gflops": round(2.0 * A.nnz * args.reps / (avg_launch * 1e-3) / 1e9, 3),
         "roofline": {"bound": "hbm", "achieved": round(B_spmv / (spmv_ms * 1e-3) / 1e9, 3),

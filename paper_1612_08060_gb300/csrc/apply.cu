@@ -33,6 +33,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -134,15 +135,49 @@ __device__ __forceinline__ double ldx(const double *p)
     if (INKERNEL) return *p;
     return ld_keep_f64(p, policy_evict_last());
 }
+__device__ __forceinline__ float ld_keep_f32(const float *p, uint64_t pol)
+{
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+template <bool INKERNEL>
+__device__ __forceinline__ float ldx(const float *p)
+{
+    if (INKERNEL) return *p;
+    return ld_keep_f32(p, policy_evict_last());
+}
+
+// binary32 -> binary64, exact, from the two formats' field layouts (IEEE 754:
+// sign | 8-bit exponent biased by 127 | 23 fraction bits, and sign | 11-bit
+// exponent biased by 1023 | 52 fraction bits).  A normal number keeps its sign,
+// its exponent gains 1023 - 127 = 896 and its fraction moves up 29 bits: a few
+// integer operations instead of a conversion instruction, which GB300 runs at
+// its (low) FP64 rate.  Zero keeps its sign; subnormals, infinities and NaNs
+// take the conversion instruction.
+__device__ __noinline__ double f2d_rare(float f)
+{
+    return (double)f;  // a call, so that the common path does not execute it predicated
+}
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t m = u & 0x7fffffffu;
+    if (m - 0x00800000u < 0x7f000000u)  // exponent field 1..254
+        return __hiloint2double((int)((u & 0x80000000u) | ((m >> 3) + 0x38000000u)),
+                                (int)(m << 29));
+    if (m == 0) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return f2d_rare(f);
+}
 
 // Batched element loop over [b, e): U independent index loads, then U
 // independent data loads, then U stores, per thread and step.
-template <int U, class LoadIdx, class LoadVal, class Store>
+template <int U, class T = double, class LoadIdx, class LoadVal, class Store>
 __device__ __forceinline__ void batched(int b, int e, int tid, LoadIdx li, LoadVal lv, Store st)
 {
     for (int base = b + tid; base < e; base += NT * U) {
         uint32_t ix[U];
-        double vv[U];
+        T vv[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int k = base + u * NT;
@@ -169,13 +204,35 @@ struct Csr3 {
     const float *val32;
 };
 
-template <bool INKERNEL>
-__device__ __forceinline__ double load_x(uint32_t c, const double *x, const double *bll,
-                                         const double *bnl)
+template <bool INKERNEL, class XT>
+__device__ __forceinline__ XT load_x(uint32_t c, const XT *x, const XT *bll, const XT *bnl)
 {
     const uint32_t blk = c >> kBlockShift;
-    const double *src = blk == 0 ? x : (blk == 1 ? bll : bnl);
+    const XT *src = blk == 0 ? x : (blk == 1 ? bll : bnl);
     return ldx<INKERNEL>(src + (c & kIndexMask));
+}
+
+// One stored entry into a row's sum.  FP64: one FMA.  FP32 values: the FP32
+// product of the value and x rounded to FP32 (already FP32 when the sources
+// hold FP32 copies), added in FP64.
+template <class XT>
+__device__ __forceinline__ double f32_product(float a, XT xv)
+{
+    float xf;
+    if constexpr (sizeof(XT) == 4) xf = xv;
+    else xf = __double2float_rn(xv);
+    return f2d_exact(__fmul_rn(a, xf));
+}
+template <bool F32, class XT>
+__device__ __forceinline__ double entry_add(double acc, const double *val, const float *val32,
+                                            int k, XT xv)
+{
+    if constexpr (F32) {
+        return __dadd_rn(acc, f32_product(val32[k], xv));
+    } else {
+        static_assert(sizeof(XT) == 8, "FP64 values take FP64 sources");
+        return fma(val[k], xv, acc);
+    }
 }
 
 // Scaling of a row result: exact exponent arithmetic when scale is a power
@@ -187,7 +244,7 @@ struct Scale {
 constexpr int kNoPow2 = 1 << 30;
 __device__ __forceinline__ double apply_scale(double acc, const Scale sc)
 {
-    if (sc.s == 1.0) return acc;
+    if (sc.e2 == 0) return acc;  // scale 1 = 2^0 (an integer test: no FP64 compare per row)
     if (sc.e2 != kNoPow2) {
         const long long bits = __double_as_longlong(acc);
         const int ex = (int)((bits >> 52) & 0x7ff);
@@ -232,13 +289,14 @@ struct StageLayout {  // byte offsets inside one stage
     int rows, col, val, bytes;
 };
 __host__ __device__ __forceinline__ int align16(int b) { return (b + 15) & ~15; }
-__host__ __device__ __forceinline__ StageLayout stage_layout(int cap, int tile_rows)
+// vb: bytes per stored value (8 FP64, 4 FP32)
+__host__ __device__ __forceinline__ StageLayout stage_layout(int cap, int tile_rows, int vb = 8)
 {
     StageLayout L;
     L.rows = 0;
     L.col = align16(4 * (tile_rows + 8));
     L.val = L.col + align16(4 * (cap + 8));
-    L.bytes = L.val + align16(8 * (cap + 8));
+    L.bytes = L.val + align16(vb * (cap + 8));
     return L;
 }
 constexpr int kMaxStages = 4;
@@ -295,9 +353,10 @@ struct TileStage {
     double *val;  // FP32 mode stores floats here
 };
 
-__device__ __forceinline__ TileStage tile_stage(unsigned char *base, int s, int cap, int tile_rows)
+__device__ __forceinline__ TileStage tile_stage(unsigned char *base, int s, int cap, int tile_rows,
+                                               int vb = 8)
 {
-    const StageLayout L = stage_layout(cap, tile_rows);
+    const StageLayout L = stage_layout(cap, tile_rows, vb);
     unsigned char *p = base + kMbarBytes + s * L.bytes;
     TileStage t;
     t.bar = reinterpret_cast<uint64_t *>(base + 16 * s);
@@ -354,11 +413,13 @@ __device__ __forceinline__ bool tile_wait(const TileStage &st, uint32_t parity, 
 // part (REMOTE: the FMA chain continues from the partial in y, then scales).
 enum SpmvMode { kFull = 0, kLocal = 1, kRemote = 2 };
 
-// Rows [r0, r1) from a staged tile.
-template <int V, bool F32, bool INKERNEL, int MODE = kFull>
-__device__ __forceinline__ void tile_compute(const TileStage &st, const double *x, const double *bll,
-                                             const double *bnl, double *y, const Scale sc, int r0,
-                                             int r1, int k0, int tid)
+// Rows [r0, r1) from a staged tile.  XT: element type of the three sources
+// (FP32 copies in the phased engines' FP32 mode).  y32, when not null, receives
+// each finished row rounded to FP32 (the next chained apply's source).
+template <int V, bool F32, bool INKERNEL, int MODE = kFull, class XT = double>
+__device__ __forceinline__ void tile_compute(const TileStage &st, const XT *x, const XT *bll,
+                                             const XT *bnl, double *y, float *y32, const Scale sc,
+                                             int r0, int r1, int k0, int tid)
 {
     const int rb = r0 & ~3, kb = k0 & ~3;
     const int nr = r1 - r0;
@@ -371,37 +432,39 @@ __device__ __forceinline__ void tile_compute(const TileStage &st, const double *
         if (i < nr) {
             const int s = st.rows[r0 - rb + i] - kb, e = st.rows[r0 - rb + i + 1] - kb;
 #pragma unroll 8
-            for (int k = s + lane; k < e; k += V) {
-                const double xv = load_x<INKERNEL>(st.col[k], x, bll, bnl);
-                if (F32)
-                    acc = __dadd_rn(acc, (double)__fmul_rn(val32[k], __double2float_rn(xv)));
-                else
-                    acc = fma(st.val[k], xv, acc);
-            }
+            for (int k = s + lane; k < e; k += V)
+                acc = entry_add<F32>(acc, st.val, val32, k, load_x<INKERNEL>(st.col[k], x, bll, bnl));
         }
         if (V > 1) {
 #pragma unroll
             for (int o = V / 2; o > 0; o >>= 1)
                 acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
         }
-        if (i < nr && lane == 0) y[r0 + i] = MODE == kLocal ? acc : apply_scale(acc, sc);
+        if (i < nr && lane == 0) {
+            if (MODE == kLocal) {
+                y[r0 + i] = acc;
+            } else {
+                const double r = apply_scale(acc, sc);
+                y[r0 + i] = r;
+                if (y32) y32[r0 + i] = __double2float_rn(r);
+            }
+        }
     }
 }
 
 // A single row with more stored entries than a stage holds: read straight from
 // global memory, the whole CTA on the row (fixed strides, fixed-order tree).
-template <bool F32, bool INKERNEL, int MODE = kFull>
-__device__ void row_direct(const Csr3 &A, const double *x, const double *bll, const double *bnl,
-                           double *y, const Scale sc, int r0, int r1, double *red, int tid)
+template <bool F32, bool INKERNEL, int MODE = kFull, class XT = double>
+__device__ void row_direct(const Csr3 &A, const XT *x, const XT *bll, const XT *bnl, double *y,
+                           float *y32, const Scale sc, int r0, int r1, double *red, int tid)
 {
     for (int i = r0; i < r1; i++) {
         const int s = ld_stream_s32(A.rowptr + i), e = ld_stream_s32(A.rowptr + i + 1);
         double acc = 0.0;
         for (int k = s + tid; k < e; k += NT) {
-            const double xv = load_x<INKERNEL>(ld_stream_u32(A.colenc + k), x, bll, bnl);
-            if (F32)
-                acc = __dadd_rn(acc, (double)__fmul_rn(ld_stream_f32(A.val32 + k),
-                                                       __double2float_rn(xv)));
+            const XT xv = load_x<INKERNEL>(ld_stream_u32(A.colenc + k), x, bll, bnl);
+            if constexpr (F32)
+                acc = __dadd_rn(acc, f32_product(ld_stream_f32(A.val32 + k), xv));
             else
                 acc = fma(ld_stream_f64(A.val + k), xv, acc);
         }
@@ -412,7 +475,13 @@ __device__ void row_direct(const Csr3 &A, const double *x, const double *bll, co
         if (tid == 0) {
             double t = MODE == kRemote ? y[i] : 0.0;
             for (int q = 0; q < NT / 32; q++) t = __dadd_rn(t, red[q]);
-            y[i] = MODE == kLocal ? t : apply_scale(t, sc);
+            if (MODE == kLocal) {
+                y[i] = t;
+            } else {
+                const double r = apply_scale(t, sc);
+                y[i] = r;
+                if (y32) y32[i] = __double2float_rn(r);
+            }
         }
         __syncthreads();
     }
@@ -420,13 +489,15 @@ __device__ void row_direct(const Csr3 &A, const double *x, const double *bll, co
 
 // Shared memory of the apply kernels: the mbarriers, `ns` stages, and a small
 // reduction area for row_direct.
-__host__ __device__ __forceinline__ int tile_smem_bytes(int cap, int tile_rows, int ns)
+__host__ __device__ __forceinline__ int tile_smem_bytes(int cap, int tile_rows, int ns, int vb = 8)
 {
-    return kMbarBytes + ns * stage_layout(cap, tile_rows).bytes + 8 * (NT / 32);
+    return kMbarBytes + ns * stage_layout(cap, tile_rows, vb).bytes + 8 * (NT / 32);
 }
-__device__ __forceinline__ double *tile_red(unsigned char *base, int cap, int tile_rows, int ns)
+__device__ __forceinline__ double *tile_red(unsigned char *base, int cap, int tile_rows, int ns,
+                                            int vb = 8)
 {
-    return reinterpret_cast<double *>(base + kMbarBytes + ns * stage_layout(cap, tile_rows).bytes);
+    return reinterpret_cast<double *>(base + kMbarBytes +
+                                      ns * stage_layout(cap, tile_rows, vb).bytes);
 }
 __device__ __forceinline__ void tile_smem_init(unsigned char *base, int ns)
 {
@@ -584,38 +655,39 @@ __device__ __noinline__ void item_signal(const Job &J, const Item &it)
     }
 }
 
-// The element work of the message steps (shared by both engines).
-template <bool INKERNEL, int U>
-__device__ __noinline__ void step_gather(double *dst, const double *src, const int32_t *idx,
-                                            int b, int e, int tid)
+// The element work of the message steps (shared by both engines; T = double,
+// or float for the FP32 copies of the phased engines' FP32 mode).
+template <bool INKERNEL, int U, class T = double>
+__device__ __noinline__ void step_gather(T *dst, const T *src, const int32_t *idx, int b, int e,
+                                         int tid)
 {
     const uint64_t pol = policy_evict_first();
-    batched<U>(
+    batched<U, T>(
         b, e, tid, [&](int k) { return (uint32_t)ld_stream_hint_s32(idx + k, pol); },
         [&](int, uint32_t j) { return ldx<INKERNEL>(src + j); },
-        [&](int k, uint32_t, double v) { dst[k] = v; });
+        [&](int k, uint32_t, T v) { dst[k] = v; });
 }
-template <bool INKERNEL, int U>
-__device__ __noinline__ void step_pack(double *gsend, const double *x, const double *lbuf,
-                                          const uint32_t *src, int b, int e, int tid)
+template <bool INKERNEL, int U, class T = double>
+__device__ __noinline__ void step_pack(T *gsend, const T *x, const T *lbuf, const uint32_t *src,
+                                       int b, int e, int tid)
 {
     const uint64_t pol = policy_evict_first();
-    batched<U>(
+    batched<U, T>(
         b, e, tid, [&](int k) { return ld_stream_hint_u32(src + k, pol); },
         [&](int, uint32_t u) {
             return (u & kFromLbuf) ? ldx<INKERNEL>(lbuf + (u & ~kFromLbuf)) : ldx<INKERNEL>(x + u);
         },
-        [&](int k, uint32_t, double v) { gsend[k] = v; });
+        [&](int k, uint32_t, T v) { gsend[k] = v; });
 }
-template <bool INKERNEL, int U>
-__device__ __noinline__ void step_transfer(double *grecv, const double *gsend,
-                                              const int32_t *dst, int b, int e, int tid)
+template <bool INKERNEL, int U, class T = double>
+__device__ __noinline__ void step_transfer(T *grecv, const T *gsend, const int32_t *dst, int b,
+                                           int e, int tid)
 {
     const uint64_t pol = policy_evict_first();
-    batched<U>(
+    batched<U, T>(
         b, e, tid, [&](int k) { return (uint32_t)ld_stream_hint_s32(dst + k, pol); },
         [&](int k, uint32_t) { return ldx<INKERNEL>(gsend + k); },
-        [&](int, uint32_t d, double v) { grecv[d] = v; });
+        [&](int, uint32_t d, T v) { grecv[d] = v; });
 }
 
 __device__ __forceinline__ bool staged_tile(const Item &it, int cap)
@@ -705,9 +777,12 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
                 const TileStage st = tile_stage(smem, cur, cap, trows);
                 const bool ok = tile_wait(st, (phase >> cur) & 1, J.err);
                 phase ^= 1u << cur;
-                if (ok) tile_compute<V, F32, true>(st, x, J.bll, J.bnl, y, J.scale, it.b, it.e, it.k0, tid);
+                if (ok)
+                    tile_compute<V, F32, true>(st, x, J.bll, J.bnl, y, nullptr, J.scale, it.b, it.e,
+                                               it.k0, tid);
             } else {
-                row_direct<F32, true>(J.A, x, J.bll, J.bnl, y, J.scale, it.b, it.e, red, tid);
+                row_direct<F32, true>(J.A, x, J.bll, J.bnl, y, nullptr, J.scale, it.b, it.e, red,
+                                      tid);
             }
             break;
         }
@@ -723,56 +798,71 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
 }
 
 // --------------------------------------------------------- phased engine
+template <class T>
 __global__ void __launch_bounds__(NT)
-    k_gather2(const double *x, const int32_t *bll_j, double *bll, int n_bll, const int32_t *lbuf_j,
-              double *lbuf, int n_lbuf, const int *err)
+    k_gather2(const T *x, const int32_t *bll_j, T *bll, int n_bll, const int32_t *lbuf_j, T *lbuf,
+              int n_lbuf, const int *err)
 {
     if (*(volatile const int *)err) return;  // sticky error: no work until cleared
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n_bll + n_lbuf; b += gridDim.x * per) {
         const int e = min(b + per, n_bll + n_lbuf);
-        if (b < n_bll) step_gather<false, 8>(bll, x, bll_j, b, min(e, n_bll), threadIdx.x);
+        if (b < n_bll) step_gather<false, 8, T>(bll, x, bll_j, b, min(e, n_bll), threadIdx.x);
         if (e > n_bll) {
             const int lb = max(b, n_bll) - n_bll, le = e - n_bll;
-            step_gather<false, 8>(lbuf, x, lbuf_j, lb, le, threadIdx.x);
+            step_gather<false, 8, T>(lbuf, x, lbuf_j, lb, le, threadIdx.x);
         }
     }
 }
+template <class T>
 __global__ void __launch_bounds__(NT)
-    k_pack(const double *x, const double *lbuf, const uint32_t *src, double *gsend, int n,
-           const int *err)
+    k_pack(const T *x, const T *lbuf, const uint32_t *src, T *gsend, int n, const int *err)
 {
     if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
-        step_pack<false, 8>(gsend, x, lbuf, src, b, min(b + per, n), threadIdx.x);
+        step_pack<false, 8, T>(gsend, x, lbuf, src, b, min(b + per, n), threadIdx.x);
 }
+template <class T>
 __global__ void __launch_bounds__(NT)
-    k_transfer(const double *gsend, const int32_t *dst, double *grecv, int n, const int *err)
+    k_transfer(const T *gsend, const int32_t *dst, T *grecv, int n, const int *err)
 {
     if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
-        step_transfer<false, 8>(grecv, gsend, dst, b, min(b + per, n), threadIdx.x);
+        step_transfer<false, 8, T>(grecv, gsend, dst, b, min(b + per, n), threadIdx.x);
 }
+template <class T>
 __global__ void __launch_bounds__(NT)
-    k_unpack(const double *grecv, const int32_t *src, double *bnl, int n, const int *err)
+    k_unpack(const T *grecv, const int32_t *src, T *bnl, int n, const int *err)
 {
     if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
-        step_gather<false, 8>(bnl, grecv, src, b, min(b + per, n), threadIdx.x);
+        step_gather<false, 8, T>(bnl, grecv, src, b, min(b + per, n), threadIdx.x);
+}
+// FP32 copy of an input vector (first apply of a chain in FP32 mode)
+__global__ void __launch_bounds__(NT) k_to_f32(const double *v, float *v32, int64_t n, const int *err)
+{
+    if (*(volatile const int *)err) return;
+    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
+        v32[i] = __double2float_rn(ld_stream_f64(v + i));
 }
 template <int V, bool F32, int MODE = kFull>
 __global__ void __launch_bounds__(NT)
-    k_spmv(Csr3 A, const double *x, const double *bll, const double *bnl, double *y, Scale sc,
-           const Item *tiles, int n_tiles, int cap, int trows, int ns, int *err)
+    k_spmv(Csr3 A, const void *xs, const void *blls, const void *bnls, double *y, float *y32,
+           Scale sc, const Item *tiles, int n_tiles, int cap, int trows, int ns, int *err)
 {
+    // FP32 mode: the three sources are FP32 copies
+    using XT = typename std::conditional<F32, float, double>::type;
+    const XT *x = static_cast<const XT *>(xs), *bll = static_cast<const XT *>(blls),
+             *bnl = static_cast<const XT *>(bnls);
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
     if (*(volatile const int *)err) return;  // sticky error: no work until cleared
+    constexpr int VB = F32 ? 4 : 8;
     tile_smem_init(smem, ns);
-    double *red = tile_red(smem, cap, trows, ns);
+    double *red = tile_red(smem, cap, trows, ns, VB);
     uint32_t phase = 0;
     // a contiguous block of tiles per CTA (neighbouring rows share x and the
     // receive buffers of their process, which then stay in this SM's L1);
@@ -785,7 +875,7 @@ __global__ void __launch_bounds__(NT)
             if (q >= q1) break;
             const Item it = tiles[q];
             if (staged_tile(it, cap))
-                tile_issue<F32>(A, tile_stage(smem, i, cap, trows), it.b, it.e, it.k0, it.k1);
+                tile_issue<F32>(A, tile_stage(smem, i, cap, trows, VB), it.b, it.e, it.k0, it.k1);
         }
     int cur = 0;
     for (int i = 0, q = q0; q < q1; i++, q++) {
@@ -795,15 +885,18 @@ __global__ void __launch_bounds__(NT)
             const Item ita = tiles[qa];
             const int sa = (cur + ns - 1) % ns;  // the stage tile i - 1 used
             if (staged_tile(ita, cap))
-                tile_issue<F32>(A, tile_stage(smem, sa, cap, trows), ita.b, ita.e, ita.k0, ita.k1);
+                tile_issue<F32>(A, tile_stage(smem, sa, cap, trows, VB), ita.b, ita.e, ita.k0,
+                                ita.k1);
         }
         if (staged_tile(it, cap)) {
-            const TileStage st = tile_stage(smem, cur, cap, trows);
+            const TileStage st = tile_stage(smem, cur, cap, trows, VB);
             const bool ok = tile_wait(st, (phase >> cur) & 1, err);
             phase ^= 1u << cur;
-            if (ok) tile_compute<V, F32, false, MODE>(st, x, bll, bnl, y, sc, it.b, it.e, it.k0, tid);
+            if (ok)
+                tile_compute<V, F32, false, MODE>(st, x, bll, bnl, y, y32, sc, it.b, it.e, it.k0,
+                                                  tid);
         } else {
-            row_direct<F32, false, MODE>(A, x, bll, bnl, y, sc, it.b, it.e, red, tid);
+            row_direct<F32, false, MODE>(A, x, bll, bnl, y, y32, sc, it.b, it.e, red, tid);
         }
         cur = cur + 1 == ns ? 0 : cur + 1;
         __syncthreads();
@@ -819,20 +912,23 @@ __global__ void __launch_bounds__(NT)
 // one whose gathers miss.
 constexpr int WPB = NT / 32;  // warps per CTA
 
-__host__ __device__ __forceinline__ int warp_smem_bytes(int capw, int rowsw, int ns)
+__host__ __device__ __forceinline__ int warp_smem_bytes(int capw, int rowsw, int ns, int vb = 8)
 {
-    return 16 * kMaxStages * WPB + WPB * ns * stage_layout(capw, rowsw).bytes;
+    return 16 * kMaxStages * WPB + WPB * ns * stage_layout(capw, rowsw, vb).bytes;
 }
 
 template <int V, bool F32, int MODE>
 __global__ void __launch_bounds__(NT)
-    k_spmv_w(Csr3 A, const double *x, const double *bll, const double *bnl, double *y, Scale sc,
-             const Item *tiles, int n_tiles, int capw, int rowsw, int ns, int *err)
+    k_spmv_w(Csr3 A, const void *xs, const void *blls, const void *bnls, double *y, float *y32,
+             Scale sc, const Item *tiles, int n_tiles, int capw, int rowsw, int ns, int *err)
 {
+    using XT = typename std::conditional<F32, float, double>::type;
+    const XT *x = static_cast<const XT *>(xs), *bll = static_cast<const XT *>(blls),
+             *bnl = static_cast<const XT *>(bnls);
     extern __shared__ __align__(16) unsigned char smem[];
     if (*(volatile const int *)err) return;  // sticky error: no work until cleared
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const StageLayout L = stage_layout(capw, rowsw);
+    const StageLayout L = stage_layout(capw, rowsw, F32 ? 4 : 8);
     unsigned char *mine = smem + 16 * kMaxStages * WPB + warp * ns * L.bytes;
     auto stage = [&](int s2) {
         TileStage t;
@@ -884,20 +980,24 @@ __global__ void __launch_bounds__(NT)
                     if (i < nr) {
                         const int s0 = st.rows[it.b - rb + i] - kb, e0 = st.rows[it.b - rb + i + 1] - kb;
 #pragma unroll 8
-                        for (int k = s0 + sub; k < e0; k += V) {
-                            const double xv = load_x<false>(st.col[k], x, bll, bnl);
-                            if (F32)
-                                acc = __dadd_rn(acc, (double)__fmul_rn(val32[k], __double2float_rn(xv)));
-                            else
-                                acc = fma(st.val[k], xv, acc);
-                        }
+                        for (int k = s0 + sub; k < e0; k += V)
+                            acc = entry_add<F32>(acc, st.val, val32, k,
+                                                 load_x<false>(st.col[k], x, bll, bnl));
                     }
                     if (V > 1) {
 #pragma unroll
                         for (int o = V / 2; o > 0; o >>= 1)
                             acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
                     }
-                    if (i < nr && sub == 0) y[it.b + i] = MODE == kLocal ? acc : apply_scale(acc, sc);
+                    if (i < nr && sub == 0) {
+                        if (MODE == kLocal) {
+                            y[it.b + i] = acc;
+                        } else {
+                            const double r = apply_scale(acc, sc);
+                            y[it.b + i] = r;
+                            if (y32) y32[it.b + i] = __double2float_rn(r);
+                        }
+                    }
                 }
             }
         } else {
@@ -906,10 +1006,9 @@ __global__ void __launch_bounds__(NT)
                 const int s0 = ld_stream_s32(A.rowptr + r), e0 = ld_stream_s32(A.rowptr + r + 1);
                 double acc = 0.0;
                 for (int k = s0 + lane; k < e0; k += 32) {
-                    const double xv = load_x<false>(ld_stream_u32(A.colenc + k), x, bll, bnl);
-                    if (F32)
-                        acc = __dadd_rn(acc, (double)__fmul_rn(ld_stream_f32(A.val32 + k),
-                                                               __double2float_rn(xv)));
+                    const XT xv = load_x<false>(ld_stream_u32(A.colenc + k), x, bll, bnl);
+                    if constexpr (F32)
+                        acc = __dadd_rn(acc, f32_product(ld_stream_f32(A.val32 + k), xv));
                     else
                         acc = fma(ld_stream_f64(A.val + k), xv, acc);
                 }
@@ -917,7 +1016,13 @@ __global__ void __launch_bounds__(NT)
                 for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
                 if (lane == 0) {
                     if (MODE == kRemote) acc = __dadd_rn(y[r], acc);
-                    y[r] = MODE == kLocal ? acc : apply_scale(acc, sc);
+                    if (MODE == kLocal) {
+                        y[r] = acc;
+                    } else {
+                        const double res = apply_scale(acc, sc);
+                        y[r] = res;
+                        if (y32) y32[r] = __double2float_rn(res);
+                    }
                 }
             }
         }
@@ -967,9 +1072,9 @@ napspmv_opts resolve_opts(const napspmv_plan_t *P, const napspmv_opts *o)
     return r;
 }
 
-static size_t smem_bytes(int32_t tile_nnz, int32_t tile_rows, int32_t ns = 2)
+static size_t smem_bytes(int32_t tile_nnz, int32_t tile_rows, int32_t ns = 2, int vb = 8)
 {
-    return (size_t)tile_smem_bytes(tile_nnz, tile_rows, ns);
+    return (size_t)tile_smem_bytes(tile_nnz, tile_rows, ns, vb);
 }
 
 int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t tile_nnz)
@@ -1145,8 +1250,12 @@ int ws_alloc(napspmv_plan_t *P, napspmv_ws_t *ws)
     auto al = [](double **p, int64_t n) {
         return cudaMalloc(p, sizeof(double) * (size_t)std::max<int64_t>(n, 1));
     };
+    auto alf = [](float **p, int64_t n) {
+        return cudaMalloc(p, sizeof(float) * (size_t)std::max<int64_t>(n, 1));
+    };
     if (al(&ws->bll, P->n_bll) || al(&ws->lbuf, P->n_lbuf) || al(&ws->gsend, P->n_gs) ||
         al(&ws->grecv, P->n_gs) || al(&ws->bnl, P->n_bnl) || al(&ws->xtmp, P->n) ||
+        alf(&ws->x32[0], P->n) || alf(&ws->x32[1], P->n) ||
         cudaMalloc(&ws->ctr, sizeof(unsigned long long) * ctr_count(P)) ||
         cudaMalloc(&ws->err, sizeof(int))) {
         ws_free(ws);
@@ -1162,10 +1271,11 @@ int ws_alloc(napspmv_plan_t *P, napspmv_ws_t *ws)
 void ws_free(napspmv_ws_t *ws)
 {
     void *p[] = {ws->bll, ws->lbuf, ws->gsend, ws->grecv, ws->bnl, ws->xtmp, ws->hv, ws->hw,
-                 ws->ctr, ws->err};
+                 ws->ctr, ws->err, ws->x32[0], ws->x32[1]};
     for (void *q : p)
         if (q) cudaFree(q);
     ws->bll = ws->lbuf = ws->gsend = ws->grecv = ws->bnl = ws->xtmp = ws->hv = ws->hw = nullptr;
+    ws->x32[0] = ws->x32[1] = nullptr;
     ws->ctr = nullptr;
     ws->err = nullptr;
 }
@@ -1236,6 +1346,7 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
         prm.jobs[i] = make_job(plans[i], wi, v[i], w[i], reps[i], scale ? scale[i] : 1.0, f32);
         prm.jobs[i].tbase = total;
         total += (long long)prm.jobs[i].n_items * reps[i];
+        wi->buf_f32 = 0;  // this engine's receive buffers hold FP64 values in both modes
         NAP_CUDA(cudaMemsetAsync(wi->ctr, 0, sizeof(unsigned long long) * ctr_count(plans[i]), s));
     }
     prm.total = total;
@@ -1254,8 +1365,8 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
     return NAPSPMV_OK;
 }
 
-using SpmvKernel = void (*)(Csr3, const double *, const double *, const double *, double *, Scale,
-                            const Item *, int, int, int, int, int *);
+using SpmvKernel = void (*)(Csr3, const void *, const void *, const void *, double *, float *,
+                            Scale, const Item *, int, int, int, int, int *);
 template <bool F32, int MODE>
 static SpmvKernel pick_spmv(int vec, bool warp = false)
 {
@@ -1294,8 +1405,9 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
     const int list = (warp ? 3 : 0) + (mode == kLocal ? 1 : mode == kRemote ? 2 : 0);
     L.cap = S.fit_nnz[list];
     L.rows = S.fit_rows[list];
-    L.sm = warp ? (size_t)warp_smem_bytes(L.cap, L.rows, o.stages)
-                : smem_bytes(L.cap, L.rows, o.stages);
+    const int vb = f32 ? 4 : 8;  // bytes per staged value
+    L.sm = warp ? (size_t)warp_smem_bytes(L.cap, L.rows, o.stages, vb)
+                : smem_bytes(L.cap, L.rows, o.stages, vb);
     if (mode == kLocal) {
         L.A = Csr3{P->d_rowptrL, P->d_colL, P->d_valL, f32 ? P->d_val32L : nullptr};
         L.fn = f32 ? pick_spmv<true, kLocal>(o.vec, warp) : pick_spmv<false, kLocal>(o.vec, warp);
@@ -1338,11 +1450,43 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
         L.grid = std::max(1, std::min(ctas, P->num_sms * std::max(occ - 1, 1)));
     return NAPSPMV_OK;
 }
-static void spmv_run(const SpmvLaunch &L, const double *x, const napspmv_ws_t *ws, double *y,
-                     double scale, int stages, cudaStream_t s)
+// x: the apply's input (FP64), or its FP32 copy in FP32 mode, where the
+// receive buffers hold FP32 copies too; y32 (FP32 mode, may be null) receives
+// the finished rows rounded to FP32.
+static void spmv_run(const SpmvLaunch &L, const void *x, const napspmv_ws_t *ws, double *y,
+                     float *y32, double scale, int stages, cudaStream_t s)
 {
-    L.fn<<<L.grid, NT, L.sm, s>>>(L.A, x, ws->bll, ws->bnl, y, make_scale(scale), L.tiles, L.n,
-                                  L.cap, L.rows, stages, ws->err);
+    L.fn<<<L.grid, NT, L.sm, s>>>(L.A, x, ws->bll, ws->bnl, y, y32, make_scale(scale), L.tiles,
+                                  L.n, L.cap, L.rows, stages, ws->err);
+}
+
+// The four message steps of one apply (phases 1-4) as kernels on stream s;
+// returns the number of launches.
+template <class T>
+static int64_t enqueue_messages(const napspmv_plan_t *P, const T *x, T *bll, T *lbuf, T *gsend,
+                                T *grecv, T *bnl, int *err, cudaStream_t s)
+{
+    auto grid = [&](int64_t n) {
+        return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
+                                                            (int64_t)P->num_sms * 8));
+    };
+    int64_t nk = 0;
+    if (P->n_bll + P->n_lbuf > 0) {
+        k_gather2<T><<<grid(P->n_bll + P->n_lbuf), NT, 0, s>>>(
+            x, P->lists[L_BLL].d_idx, bll, (int)P->n_bll, P->lists[L_LBUF].d_idx, lbuf,
+            (int)P->n_lbuf, err);
+        nk++;
+    }
+    if (P->n_gs > 0) {
+        k_pack<T><<<grid(P->n_gs), NT, 0, s>>>(x, lbuf, P->d_pack_src, gsend, (int)P->n_gs, err);
+        k_transfer<T><<<grid(P->n_gs), NT, 0, s>>>(gsend, P->d_xfer_dst, grecv, (int)P->n_gs, err);
+        nk += 2;
+    }
+    if (P->n_bnl > 0) {
+        k_unpack<T><<<grid(P->n_bnl), NT, 0, s>>>(grecv, P->d_unp_src, bnl, (int)P->n_bnl, err);
+        nk++;
+    }
+    return nk;
 }
 
 static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
@@ -1360,42 +1504,45 @@ static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, 
         if (int rc = spmv_launch(P, o, kLocal, LL)) return rc;
         if (int rc = spmv_launch(P, o, kRemote, LR)) return rc;
     }
+    // FP32 mode: the message steps move FP32 copies (the products round x to
+    // FP32 anyway), the SpMV reads FP32 sources, and each apply's SpMV also
+    // writes the FP32 copy of its result for the next apply of the chain
+    const bool f32 = o.precision == NAPSPMV_PREC_F32;
     int64_t nk = 0;
+    if (f32) {
+        k_to_f32<<<grid(P->n), NT, 0, s>>>(v, ws->x32[0], P->n, ws->err);
+        nk++;
+    }
+    ws->buf_f32 = f32 ? 1 : 0;
     for (int k = 0; k < reps; k++) {
         const double *x = (k == 0) ? v : (((reps - k) & 1) == 0 ? w : ws->xtmp);
         double *y = (((reps - 1 - k) & 1) == 0) ? w : ws->xtmp;
+        float *x32 = ws->x32[k & 1];
+        float *y32 = (f32 && k + 1 < reps) ? ws->x32[(k + 1) & 1] : nullptr;
+        const void *xs = f32 ? (const void *)x32 : (const void *)x;
         if (overlap) {
             // Algorithm NAPSpMV: local_spmv(A_on_process) needs no message and
             // runs on a second stream while the message steps proceed
             NAP_CUDA(cudaEventRecord(P->ev_fork, s));
             NAP_CUDA(cudaStreamWaitEvent(P->aux, P->ev_fork, 0));
-            spmv_run(LL, x, ws, y, scale, o.stages, P->aux);
+            spmv_run(LL, xs, ws, y, nullptr, scale, o.stages, P->aux);
             nk++;
             NAP_CUDA(cudaEventRecord(P->ev_join, P->aux));
         }
-        if (P->n_bll + P->n_lbuf > 0) {
-            k_gather2<<<grid(P->n_bll + P->n_lbuf), NT, 0, s>>>(
-                x, P->lists[L_BLL].d_idx, ws->bll, (int)P->n_bll, P->lists[L_LBUF].d_idx, ws->lbuf,
-                (int)P->n_lbuf, ws->err);
-            nk++;
-        }
-        if (P->n_gs > 0) {
-            k_pack<<<grid(P->n_gs), NT, 0, s>>>(x, ws->lbuf, P->d_pack_src, ws->gsend, (int)P->n_gs,
-                                                ws->err);
-            k_transfer<<<grid(P->n_gs), NT, 0, s>>>(ws->gsend, P->d_xfer_dst, ws->grecv,
-                                                    (int)P->n_gs, ws->err);
-            nk += 2;
-        }
-        if (P->n_bnl > 0) {
-            k_unpack<<<grid(P->n_bnl), NT, 0, s>>>(ws->grecv, P->d_unp_src, ws->bnl, (int)P->n_bnl,
-                                                   ws->err);
-            nk++;
-        }
+        if (f32)
+            nk += enqueue_messages<float>(P, x32, reinterpret_cast<float *>(ws->bll),
+                                          reinterpret_cast<float *>(ws->lbuf),
+                                          reinterpret_cast<float *>(ws->gsend),
+                                          reinterpret_cast<float *>(ws->grecv),
+                                          reinterpret_cast<float *>(ws->bnl), ws->err, s);
+        else
+            nk += enqueue_messages<double>(P, x, ws->bll, ws->lbuf, ws->gsend, ws->grecv, ws->bnl,
+                                           ws->err, s);
         if (overlap) {
             NAP_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
-            spmv_run(LR, x, ws, y, scale, o.stages, s);
+            spmv_run(LR, xs, ws, y, y32, scale, o.stages, s);
         } else {
-            spmv_run(LF, x, ws, y, scale, o.stages, s);
+            spmv_run(LF, xs, ws, y, y32, scale, o.stages, s);
         }
         nk++;
         NAP_CUDA(cudaGetLastError());
@@ -1679,10 +1826,25 @@ extern "C" int napspmv_spmv_step(napspmv_plan_t *P, napspmv_ws_t *ws, const doub
     NAP_CUDA(cudaGetDevice(&cur));
     if (cur != P->device) NAP_CUDA(cudaSetDevice(P->device));
     if ((rc = build_items(P, o.chunk, o.tile_rows, o.tile_nnz))) return rc;
+    const bool f32 = o.precision == NAPSPMV_PREC_F32;
+    if (W->buf_f32 != (f32 ? 1 : 0)) {
+        set_error(NAPSPMV_ERR_STATE, "the receive buffers hold the other precision's copies: "
+                                     "apply once in this precision (phased or overlapped engine "
+                                     "for FP32) before the step");
+        return NAPSPMV_ERR_STATE;
+    }
     SpmvLaunch L;
     if ((rc = spmv_launch(P, o, kFull, L))) return rc;
-    spmv_run(L, v, W, w, scale, o.stages, (cudaStream_t)stream);
-    count_launch(1);
+    if (f32) {
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((P->n + NT - 1) / NT,
+                                                                  (int64_t)P->num_sms * 8));
+        k_to_f32<<<g, NT, 0, (cudaStream_t)stream>>>(v, W->x32[0], P->n, W->err);
+        spmv_run(L, W->x32[0], W, w, nullptr, scale, o.stages, (cudaStream_t)stream);
+        count_launch(2);
+    } else {
+        spmv_run(L, v, W, w, nullptr, scale, o.stages, (cudaStream_t)stream);
+        count_launch(1);
+    }
     NAP_CUDA(cudaGetLastError());
     if (cur != P->device) cudaSetDevice(cur);
     return NAPSPMV_OK;

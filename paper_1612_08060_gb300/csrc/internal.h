@@ -94,6 +94,11 @@ struct napspmv_ws_s {
     int device = 0;
     double *bll = nullptr, *lbuf = nullptr, *gsend = nullptr, *grecv = nullptr, *bnl = nullptr;
     double *xtmp = nullptr;            // chained-apply intermediate vector
+    // FP32 mode of the phased engines: FP32 copies of the chain's vectors, and
+    // whether the receive buffers hold FP32 copies (their contents are then
+    // read as float arrays)
+    float *x32[2] = {nullptr, nullptr};
+    int buf_f32 = 0;
     double *hv = nullptr, *hw = nullptr;  // staging of napspmv_apply_host
     unsigned long long *ctr = nullptr;  // ticket + kNumCounters * nn
     int *err = nullptr;                 // sticky device status

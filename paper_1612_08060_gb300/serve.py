@@ -43,9 +43,10 @@ class Matrix:
         self.build_s = time.perf_counter() - t0
         st = nap.napspmv_plan_stats(self.plan)
         bufs = st["bll_total"] + st["lbuf_total"] + 2 * st["nap_inter_vals"] + st["bnl_total"]
-        # matrix (col, values FP64 + FP32, row pointer) + index arrays + one workspace
-        self.plan_bytes = A.nnz * 16 + A.n * 12 + bufs * 12 + 8 * A.n
-        self.ws_bytes = bufs * 8 + A.n * 8
+        # matrix (col, values FP64 + FP32, row pointer) + index arrays + one
+        # workspace (receive buffers, chain vector, two FP32 vector copies)
+        self.plan_bytes = A.nnz * 16 + A.n * 12 + bufs * 12 + 16 * A.n
+        self.ws_bytes = bufs * 8 + A.n * 16
         self.users = 0
 
 

@@ -127,6 +127,41 @@ def test_engines_agree_bitwise(reps):
     assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("reps", [1, 3])
+def test_engines_agree_bitwise_fp32(reps):
+    """FP32 values: the fused engine rounds each gathered FP64 x to FP32 at the
+    product; the phased engines carry FP32 copies of the same values through
+    the message steps.  Same floats, same chain order: identical bits."""
+    A = I.aniso_q1(64)
+    v = I.vector(A.n, 22)
+    plan = gpu_plan(A, 16, 4)
+    o = dict(reps=reps, scale=0.25, vec=1, precision=nap.PREC_F32)
+    a = run(plan, v, engine=nap.ENGINE_FUSED, **o)
+    b = run(plan, v, engine=nap.ENGINE_PHASED, **o)
+    c = run(plan, v, engine=nap.ENGINE_OVERLAP, **o)
+    d = run(plan, v, engine=nap.ENGINE_OVERLAP, pipeline=nap.PIPELINE_WARP, **o)
+    assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, d)
+
+
+@pytest.mark.parametrize("eng", ENGINES)
+def test_fp32_product_special_values(eng):
+    """Rows of one entry: w_i is the FP32 product itself, widened to FP64 (0 +
+    p).  Products that are normal, subnormal, +-0, +-inf or NaN must widen
+    exactly as the oracle's (C) conversion does: compared bit for bit."""
+    a = np.array([1.5, 1e-30, 3.0, -2.0, 1e30, -1e30, 0.0, 2.0 ** -126, 7.0, 1.0, 0.5, 1.0],
+                 np.float32)
+    x = np.array([0.1, 1e-15, -0.0, 0.0, 1e30, 1e30, np.inf, 0.75, 1.0 / 3.0, np.nan,
+                  2.0 ** -140, -3.4e38])
+    n = len(a)
+    A = I.CSR(np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), a.astype(np.float64))
+    w = run(gpu_plan(A, 4, 2), x, precision=nap.PREC_F32, **eng)
+    with np.errstate(all="ignore"):
+        ref = O.spmv_f32(A.row_ptr, A.col, a, x)
+    assert np.array_equal(np.isnan(w), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert np.array_equal(w[ok].view(np.uint64), ref[ok].view(np.uint64)), (w, ref)
+
+
 def test_host_entry_point():
     A = I.poisson2d(40)
     v = I.vector(A.n, 4)
