@@ -135,6 +135,24 @@ __device__ __forceinline__ double ldx(const double *p)
     if (INKERNEL) return *p;
     return ld_keep_f64(p, policy_evict_last());
 }
+// The local pass's partial row sums: stored L2-resident (evict last) for the
+// remote pass, which reads them once more (evict first: the line is about to
+// be overwritten with the finished row).
+__device__ __forceinline__ void st_partial_f64(double *p, double v)
+{
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v),
+                 "l"(policy_evict_last())
+                 : "memory");
+}
+__device__ __forceinline__ double ld_partial_f64(const double *p)
+{
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;"
+                 : "=d"(v)
+                 : "l"(p), "l"(policy_evict_first())
+                 : "memory");
+    return v;
+}
 __device__ __forceinline__ float ld_keep_f32(const float *p, uint64_t pol)
 {
     float v;
@@ -428,7 +446,7 @@ __device__ __forceinline__ void tile_compute(const TileStage &st, const XT *x, c
     for (int base = 0; base < nr; base += groups) {
         const int i = base + grp;
         double acc = 0.0;
-        if (MODE == kRemote && i < nr && lane == 0) acc = y[r0 + i];
+        if (MODE == kRemote && i < nr && lane == 0) acc = ld_partial_f64(y + r0 + i);
         if (i < nr) {
             const int s = st.rows[r0 - rb + i] - kb, e = st.rows[r0 - rb + i + 1] - kb;
 #pragma unroll 8
@@ -442,7 +460,7 @@ __device__ __forceinline__ void tile_compute(const TileStage &st, const XT *x, c
         }
         if (i < nr && lane == 0) {
             if (MODE == kLocal) {
-                y[r0 + i] = acc;
+                st_partial_f64(y + r0 + i, acc);
             } else {
                 const double r = apply_scale(acc, sc);
                 y[r0 + i] = r;
@@ -976,7 +994,7 @@ __global__ void __launch_bounds__(NT)
                 for (int base = 0; base < nr; base += 32 / V) {
                     const int i = base + grp;
                     double acc = 0.0;
-                    if (MODE == kRemote && i < nr && sub == 0) acc = y[it.b + i];
+                    if (MODE == kRemote && i < nr && sub == 0) acc = ld_partial_f64(y + it.b + i);
                     if (i < nr) {
                         const int s0 = st.rows[it.b - rb + i] - kb, e0 = st.rows[it.b - rb + i + 1] - kb;
 #pragma unroll 8
@@ -991,7 +1009,7 @@ __global__ void __launch_bounds__(NT)
                     }
                     if (i < nr && sub == 0) {
                         if (MODE == kLocal) {
-                            y[it.b + i] = acc;
+                            st_partial_f64(y + it.b + i, acc);
                         } else {
                             const double r = apply_scale(acc, sc);
                             y[it.b + i] = r;
