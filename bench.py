@@ -191,6 +191,18 @@ def bytes_per_apply(A, st):
     return b_csr + b_msg
 
 
+def modelled_comm(nap, plan, w):
+    """Sec. 3 cost models (max-rate inter-node, intra-node) with the paper's
+    Blue Waters parameters, applied to this plan's messages: the modelled
+    communication time of one standard and one node-aware exchange."""
+    from paper_1612_08060_gb300 import model
+    lists = {k: nap.export_list(plan, getattr(nap, "LIST_" + k))[:3]
+             for k in ("STD", "INTER", "J0", "J1", "J2")}
+    m = model.modelled(lists, w.ppn, w.n_p)
+    return {k: float(f"{v:.4g}") for k, v in m.items()} | {
+        "machine": "Blue Waters parameters of Sec. 3 (not this GPU)"}
+
+
 def cpu_baseline_leg(A, v, w_gpu_one, B, budget_s):
     """The oracle timed on this host's cores on a bounded sample, and the
     relative error of one GPU apply against it."""
@@ -417,6 +429,7 @@ def main():
                  "std_inter_msgs": st["std_inter_msgs"], "std_inter_vals": st["std_inter_vals"],
                  "nap_inter_msgs": st["nap_inter_msgs"], "nap_inter_vals": st["nap_inter_vals"],
                  "nap_intra_msgs": st["nap_intra_msgs"], "nap_intra_vals": st["nap_intra_vals"]},
+        "modelled_comm": modelled_comm(nap, plan, w),
         "e2e": e2e,
         "clocks": clocks,
     }

@@ -11,6 +11,8 @@
  * follows a definition of the paper, evaluated by plain enumeration:
  *
  *   orc_row_start / orc_owner   Sec. 2, Eqs. R and R_pn (row partition)
+ *   strided partition           Sec. 5 (SuiteSparse runs): row i on rank
+ *                               i mod n_p (flag ORC_STRIDED)
  *   classification              Sec. 2, Eqs. on_proc, off_proc, on_node,
  *                               off_node
  *   STD list                    Sec. 2.1, Eqs. P and D
@@ -64,6 +66,7 @@
 #define ORC_ERR_PLAN (-7) /* a value the algorithm needs was never delivered */
 
 #define ORC_MAP_TEXT 2 /* same bit as the library's flag, chosen independently */
+#define ORC_STRIDED 4  /* row i belongs to rank i mod n_p (Sec. 5's strided partition) */
 
 enum { L_STD = 0, L_NODE, L_INTER, L_J0, L_J1, L_J2, L_BLL, L_BNL, L_LBUF, L_COUNT };
 
@@ -105,6 +108,13 @@ int64_t orc_owner(int64_t n, int64_t np, int64_t j)
             hi = mid - 1;
     }
     return lo;
+}
+
+/* The owner of row / column j under the plan's partition. */
+static int64_t own(const orc_plan *P, int64_t j)
+{
+    if (P->flags & ORC_STRIDED) return j % P->np;
+    return orc_owner(P->n, P->np, j);
 }
 
 static int64_t procs_on_node(const orc_plan *P, int64_t node)
@@ -290,10 +300,10 @@ int orc_plan_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t
      * set of t; off-node ones define N and E (Eqs. N, E) and the off-node
      * receive set of t. */
     for (int64_t i = 0; i < n; i++) {
-        int64_t t = orc_owner(n, np, i);
+        int64_t t = own(P, i);
         for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
             int64_t j = col[k];
-            int64_t r = orc_owner(n, np, j);
+            int64_t r = own(P, j);
             if (r == t) {
                 P->split[3 * i + 0]++;
             } else if (r / ppn == t / ppn) {
@@ -382,7 +392,7 @@ int orc_plan_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t
             int64_t s = I->src[k];
             for (int64_t q = I->ptr[k]; q < I->ptr[k + 1]; q++) {
                 int64_t j = I->idx[q];
-                int64_t p = orc_owner(n, np, j);
+                int64_t p = own(P, j);
                 if (p != s && (tpush(&j0, p, s, j) || tpush(&lbuf, s, s, j))) {
                     rc = ORC_ERR_OOM;
                     goto done;
@@ -577,7 +587,7 @@ int orc_napspmv(const orc_plan *P, const int64_t *row_ptr, const int32_t *col,
         for (int64_t x = J2->ptr[k]; x < J2->ptr[k + 1]; x++) {
             int64_t j = J2->idx[x];
             int64_t pos = bs < 0 ? -1 : lfind(BL, bs, j);
-            if (pos < 0 || orc_owner(n, np, j) != p) { rc = ORC_ERR_PLAN; goto out; }
+            if (pos < 0 || own(P, j) != p) { rc = ORC_ERR_PLAN; goto out; }
             bll[pos] = v[j];
         }
     }
@@ -588,7 +598,7 @@ int orc_napspmv(const orc_plan *P, const int64_t *row_ptr, const int32_t *col,
         for (int64_t x = J0->ptr[k]; x < J0->ptr[k + 1]; x++) {
             int64_t j = J0->idx[x];
             int64_t pos = bs < 0 ? -1 : lfind(LB, bs, j);
-            if (pos < 0 || orc_owner(n, np, j) != p) { rc = ORC_ERR_PLAN; goto out; }
+            if (pos < 0 || own(P, j) != p) { rc = ORC_ERR_PLAN; goto out; }
             lbf[pos] = v[j];
         }
     }
@@ -599,7 +609,7 @@ int orc_napspmv(const orc_plan *P, const int64_t *row_ptr, const int32_t *col,
         for (int64_t x = I->ptr[k]; x < I->ptr[k + 1]; x++) {
             int64_t j = I->idx[x];
             double val_j;
-            if (orc_owner(n, np, j) == p) {
+            if (own(P, j) == p) {
                 val_j = v[j];
             } else {
                 int64_t pos = bs < 0 ? -1 : lfind(LB, bs, j);
@@ -637,12 +647,12 @@ int orc_napspmv(const orc_plan *P, const int64_t *row_ptr, const int32_t *col,
     }
     /* local_spmv over the three blocks, accumulated into w. */
     for (int64_t i = 0; i < n; i++) {
-        int64_t t = orc_owner(n, np, i);
+        int64_t t = own(P, i);
         int64_t bl = lrank(BL, t), bn = lrank(BN, t);
         double s = 0.0;
         for (int blk = 0; blk < 3; blk++) {
             for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
-                int64_t j = col[k], r = orc_owner(n, np, j);
+                int64_t j = col[k], r = own(P, j);
                 int b = (r == t) ? 0 : (r / P->ppn == t / P->ppn ? 1 : 2);
                 if (b != blk) continue;
                 double x;

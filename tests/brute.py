@@ -9,8 +9,11 @@ oracle's header).  Nothing here is fast or clever on purpose.
 from __future__ import annotations
 
 
-def partition(n, n_p):
-    """R(r) as explicit sets; the first n mod n_p ranks get one more row."""
+def partition(n, n_p, strided=False):
+    """R(r) as explicit sets; the first n mod n_p ranks get one more row.
+    strided: R(r) = {i : i mod n_p = r} (the strided partition of Sec. 5)."""
+    if strided:
+        return [set(range(r, n, n_p)) for r in range(n_p)]
     q, rem = divmod(n, n_p)
     R, start = [], 0
     for r in range(n_p):
@@ -20,12 +23,12 @@ def partition(n, n_p):
     return R
 
 
-def brute_plan(n, rows, n_p, ppn, map_text=False):
+def brute_plan(n, rows, n_p, ppn, map_text=False, strided=False):
     """rows[i] = set of stored columns of row i.  Returns a dict of dicts:
     STD/J0/J1/J2/INTER: {(src, dst): sorted tuple}; NODE: {(n, m): tuple};
     BLL/BNL/LBUF: {rank: tuple}; T, U: {rank: set of nodes}; G: {rank: set};
     split: list of (on_process, on_node, off_node) counts per row."""
-    R = partition(n, n_p)
+    R = partition(n, n_p, strided)
     nn = (n_p + ppn - 1) // ppn
     node_ranks = [[r for r in range(n_p) if r // ppn == x] for x in range(nn)]
     node_rows = [set().union(*(R[r] for r in node_ranks[x])) for x in range(nn)]

@@ -91,3 +91,56 @@ def test_invariants_random():
                 assert a != b and a // ppn == b // ppn
         for (a, b) in itertools.chain(D, inter):
             assert a != b
+
+
+@pytest.mark.parametrize("n,dens,seed,n_p,ppn", CASES[::2])
+def test_strided_plans_match_set_definitions(n, dens, seed, n_p, ppn):
+    """The strided partition (row i on rank i mod n_p, Sec. 5): every list,
+    layout and row split against the literal set evaluation."""
+    A = random_pattern(n, dens, seed)
+    plan = O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=O.STRIDED)
+    b = brute_plan(n, _rows(A), n_p, ppn, strided=True)
+    for name, kind in LISTS:
+        assert plan.list_dict(kind) == b[name], name
+    for name, kind in LAYOUTS:
+        got = {s: idx for (s, d), idx in plan.list_dict(kind).items()}
+        assert got == b[name], name
+    assert [tuple(r) for r in plan.split().tolist()] == b["split"]
+
+
+@pytest.mark.parametrize("n,dens,seed,n_p,ppn", CASES[1::4])
+def test_strided_napspmv_equals_dense(n, dens, seed, n_p, ppn):
+    A = random_pattern(n, dens, seed)
+    v = np.random.default_rng(seed + 200).uniform(-1, 1, n)
+    ref = A.to_dense() @ v
+    scale = np.abs(A.to_dense()) @ np.abs(v)
+    plan = O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=O.STRIDED)
+    w = plan.napspmv(A.row_ptr, A.col, A.val, v)
+    assert np.all(np.abs(w - ref) <= 4 * np.finfo(float).eps * scale + 1e-300)
+
+
+@pytest.mark.parametrize("n_p,ppn,k", [(5, 2, 4), (8, 4, 3), (12, 3, 5), (3, 1, 7)])
+def test_strided_tridiagonal_closed_form(n_p, ppn, k):
+    """1D 3-point operator, n = k n_p.  Strided: row i (rank i mod n_p) needs
+    i-1 from rank (t-1) mod n_p and i+1 from rank (t+1) mod n_p, so every rank
+    receives two messages; |D((t-1) mod n_p, t)| = k, one less when that sender
+    is rank n_p-1 (column n-1 is not needed to the left), and |D((t+1) mod
+    n_p, t)| = k, one less when the sender is rank 0 (column 0 is not needed
+    to the right): 2 n_p messages carrying 2n - 2 values.  Contiguous: only
+    the 2 (n_p - 1) block boundaries communicate, one value each."""
+    n = k * n_p
+    rows = [[j for j in (i - 1, i, i + 1) if 0 <= j < n] for i in range(n)]
+    rp = np.zeros(n + 1, np.int64)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([j for r in rows for j in r], np.int32)
+    D = O.OraclePlan(rp, col, n_p, ppn, flags=O.STRIDED).list_dict(O.STD)
+    want = {}
+    for t in range(n_p):
+        left, right = (t - 1) % n_p, (t + 1) % n_p
+        want[(left, t)] = k - (1 if left == n_p - 1 else 0)
+        want[(right, t)] = k - (1 if right == 0 else 0)
+    assert {key: len(v) for key, v in D.items()} == want
+    assert sum(len(v) for v in D.values()) == 2 * n - 2
+    Dc = O.OraclePlan(rp, col, n_p, ppn).list_dict(O.STD)
+    assert len(Dc) == 2 * (n_p - 1) and all(len(v) == 1 for v in Dc.values())
+
