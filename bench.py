@@ -170,7 +170,9 @@ def run_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n": A.n, "nnz": A.nnz, "n_p": w.n_p, "ppn": w.ppn,
+        "config": {"workload": w.name + ("_strided" if args.partition == "strided" else ""),
+                   "n": A.n, "nnz": A.nnz, "n_p": w.n_p, "ppn": w.ppn,
+                   "partition": args.partition,
                    "applies_per_step": 1},
         "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} plain FP64 CSR SpMVs of the full matrix, "
@@ -237,6 +239,8 @@ def main():
     ap.add_argument("--tile-nnz", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--pipeline", default="default", choices=["default", "cta", "warp"])
+    ap.add_argument("--partition", default="contiguous", choices=["contiguous", "strided"],
+                    help="strided: row i on process i mod n_p (the SuiteSparse runs' partition)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -270,7 +274,8 @@ def main():
     torch.cuda.set_device(dev)
     w, A, v = build_workload(args.config)
     t0 = time.perf_counter()
-    plan = nap.napspmv_plan(A.row_ptr, A.col, A.val, w.n_p, w.ppn, nap.F32_VALUES)
+    pflags = nap.F32_VALUES | (nap.PARTITION_STRIDED if args.partition == "strided" else 0)
+    plan = nap.napspmv_plan(A.row_ptr, A.col, A.val, w.n_p, w.ppn, pflags)
     plan_ms = (time.perf_counter() - t0) * 1e3
     st = nap.napspmv_plan_stats(plan)
     f32 = args.precision == "f32"
@@ -401,7 +406,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32-values/f64-sums" if f32 else "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n": A.n, "nnz": A.nnz, "n_p": w.n_p, "ppn": w.ppn,
+        "config": {"workload": w.name + ("_strided" if args.partition == "strided" else ""),
+                   "n": A.n, "nnz": A.nnz, "n_p": w.n_p, "ppn": w.ppn,
+                   "partition": args.partition,
                    "applies_per_step": args.reps, "scale": SCALE,
                    "engine": {1: "fused", 2: "phased", 3: "overlap"}[opts.engine or eff.engine],
                    "vec": opts.vec or eff.vec, "chunk": opts.chunk or eff.chunk,

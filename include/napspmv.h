@@ -66,6 +66,13 @@ extern "C" {
  * prose after Eq. U states, instead of the default that reproduces the
  * paper's Tables U and G (ascending |E|, last process first). */
 #define NAPSPMV_MAP_TEXT (1u << 1)
+/* Strided row partition: row i belongs to process i mod n_p (the partition of
+ * the paper's SuiteSparse runs, Sec. 5) instead of contiguous blocks (Eq. R).
+ * A node's rows then interleave with every other node's, so the fused engine
+ * (whose SpMV items wait on one node's messages) is not available for such a
+ * plan: its applies return ERR_UNSUPPORTED; the phased and overlapped engines
+ * serve it. */
+#define NAPSPMV_PARTITION_STRIDED (1u << 2)
 
 /* ------------------------------------------------------------- apply modes */
 #define NAPSPMV_PREC_F64 0 /* FP64 values, FP64 products and sums            */
@@ -165,7 +172,8 @@ typedef struct {
 /* Build the plans of A for n_p simulated processes, ppn per node.
  *   A      CSR (host or device memory), see napspmv_csr.
  *   n_p    1 <= n_p <= N;  ppn >= 1 (the last node may hold fewer processes).
- *   flags  NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT.
+ *   flags  NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT | NAPSPMV_PARTITION_STRIDED;
+ *          other bits: ERR_ARG.
  *   out    receives the plan; the caller frees it with napspmv_plan_destroy.
  * Runs on the current device and synchronises it.  Errors: ERR_ARG for a
  * malformed CSR or bad n_p / ppn, ERR_UNSUPPORTED beyond the size limits,
@@ -208,7 +216,9 @@ int napspmv_apply_host(napspmv_plan_t *P, const double *v_host, double *w_host, 
 /* One persistent launch over `count` independent applies (each with its own
  * plan, workspace, vectors, reps and scale): the batched form used by the
  * request server.  ws[i] may be NULL only if no other entry uses the same
- * plan's own workspace.  count <= 64.  Fused engine only. */
+ * plan's own workspace.  count <= 64.  Fused engine (count = 1 runs as
+ * napspmv_apply_ex with the given options), so with count > 1 plans built
+ * with NAPSPMV_PARTITION_STRIDED give ERR_UNSUPPORTED. */
 int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const *ws,
                         const double *const *v, double *const *w, const int32_t *reps,
                         const double *scale, const napspmv_opts *opts, void *stream);
@@ -230,7 +240,8 @@ int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_
  *   - The first call on a device looks the array's device address up (with
  *     that device current); make that first call before any stream capture.
  *   - Uses the fused engine with the plan's current work items and FP64
- *     values; device-side timeouts are reported by napspmv_status(P). */
+ *     values (strided plans: ERR_UNSUPPORTED); device-side timeouts are
+ *     reported by napspmv_status(P). */
 int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double *w, int32_t reps,
                           double scale, void *stream);
 

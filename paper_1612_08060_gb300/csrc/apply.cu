@@ -1646,6 +1646,11 @@ static int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
         set_error(NAPSPMV_ERR_ARG, "unknown engine");
         return NAPSPMV_ERR_ARG;
     }
+    if (o.engine == NAPSPMV_ENGINE_FUSED && (P->flags & NAPSPMV_PARTITION_STRIDED)) {
+        set_error(NAPSPMV_ERR_UNSUPPORTED, "the fused engine needs contiguous node rows; a "
+                                           "strided plan runs on the phased or overlapped engine");
+        return NAPSPMV_ERR_UNSUPPORTED;
+    }
     if (o.timeout_ms < 1) {
         set_error(NAPSPMV_ERR_ARG, "timeout_ms must be >= 1");
         return NAPSPMV_ERR_ARG;
@@ -1691,6 +1696,12 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
         if (P->device != P0->device) {
             set_error(NAPSPMV_ERR_ARG, "all plans of a batch must live on one device");
             rc = NAPSPMV_ERR_ARG;
+            break;
+        }
+        if (count > 1 && (P->flags & NAPSPMV_PARTITION_STRIDED)) {
+            set_error(NAPSPMV_ERR_UNSUPPORTED, "batched applies run the fused engine, which "
+                                               "needs contiguous node rows (no strided plans)");
+            rc = NAPSPMV_ERR_UNSUPPORTED;
             break;
         }
         if ((rc = check_opts(P, o))) break;
@@ -1752,6 +1763,11 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
     if (!P || !v || !w || reps < 1 || (const double *)w == v) {
         set_error(NAPSPMV_ERR_ARG, "NULL plan or vector, reps < 1, or w == v");
         return NAPSPMV_ERR_ARG;
+    }
+    if (P->flags & NAPSPMV_PARTITION_STRIDED) {
+        set_error(NAPSPMV_ERR_UNSUPPORTED, "napspmv_apply_noalloc runs the fused engine, which "
+                                           "needs contiguous node rows (no strided plans)");
+        return NAPSPMV_ERR_UNSUPPORTED;
     }
     // doubles of scratch: counters (as 8-byte words), b_{l->l}, b_{l->nl},
     // g_send, g_recv, b_{nl->l}, the chain vector

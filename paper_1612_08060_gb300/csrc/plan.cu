@@ -85,12 +85,17 @@ inline int bits_for(int64_t maxval)  // bits to hold 0..maxval
     return b;
 }
 
-struct Part {  // row partition of Eq. R, first N mod n_p ranks one row longer
-    int64_t q, rem, big;
+// Row partition: contiguous blocks of Eq. R (first N mod n_p ranks one row
+// longer), or strided (row i on rank i mod n_p, Sec. 5).
+struct Part {
+    int64_t q, rem, big, np;
+    bool strided;
     __host__ __device__ int64_t owner(int64_t j) const
     {
+        if (strided) return j % np;
         return j < big ? j / (q + 1) : rem + (j - big) / q;
     }
+    // first row of rank r (contiguous blocks only)
     __host__ __device__ int64_t start(int64_t r) const { return r * q + (r < rem ? r : rem); }
 };
 
@@ -580,7 +585,8 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
     const int64_t n = A->n, nnz = A->nnz;
     const int32_t np = P->np, ppn = P->ppn, nn = P->nn;
     Cub cb;
-    Part part{n / np, n % np, (n % np) * (n / np + 1)};
+    Part part{n / np, n % np, (n % np) * (n / np + 1), np,
+              (P->flags & NAPSPMV_PARTITION_STRIDED) != 0};
     const int jb = bits_for(n - 1), rb = bits_for(np - 1), nb = bits_for(nn - 1);
     if (2 * rb + jb > 63)
         throw NapError{NAPSPMV_ERR_UNSUPPORTED, "N and n_p too large for 64-bit plan keys"};
@@ -917,7 +923,9 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
         P->node_bll[x] = bll_ptr[r];
         P->node_lbuf[x] = lbuf_ptr[r];
         P->node_bnl[x] = bnl_ptr[r];
-        P->node_rows[x] = part.start(r);
+        // strided: every node's rows interleave; the row tiles are cut over
+        // all rows as one range (only the phased engines run such plans)
+        P->node_rows[x] = part.strided ? (x == 0 ? 0 : n) : part.start(r);
     }
     {
         int64_t i = 0;
@@ -988,6 +996,10 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
     }
     if (np < 1 || np > A->n || ppn < 1) {
         set_error(NAPSPMV_ERR_ARG, "need 1 <= n_p <= N and ppn >= 1");
+        return NAPSPMV_ERR_ARG;
+    }
+    if (flags & ~(NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT | NAPSPMV_PARTITION_STRIDED)) {
+        set_error(NAPSPMV_ERR_ARG, "unknown plan flag");
         return NAPSPMV_ERR_ARG;
     }
     if (A->n >= (1ll << 30) || A->nnz >= (1ll << 31) - 64) {

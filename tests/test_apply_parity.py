@@ -162,6 +162,50 @@ def test_fp32_product_special_values(eng):
     assert np.array_equal(w[ok].view(np.uint64), ref[ok].view(np.uint64)), (w, ref)
 
 
+@pytest.mark.parametrize("eng", [e for e in ENGINES if e["engine"] != nap.ENGINE_FUSED])
+@pytest.mark.parametrize("n,dens,n_p,ppn", [(300, 0.02, 37, 4), (1000, 0.01, 64, 16),
+                                             (97, 0.05, 97, 3)])
+def test_strided_partition(eng, n, dens, n_p, ppn):
+    """Strided plans (row i on process i mod n_p) on the phased engines: FP64
+    and FP32-value applies, single and chained, against the oracle."""
+    A = I.random_pattern(n, dens, n + 7)
+    v = I.vector(n, 8)
+    plan = gpu_plan(A, n_p, ppn, nap.F32_VALUES | nap.PARTITION_STRIDED)
+    for vec in (1, 4):
+        w = run(plan, v, vec=vec, **eng)
+        assert_close_fp64(w, O.spmv(A.row_ptr, A.col, A.val, v), abs_row_bound(A, v))
+    w = run(plan, v, reps=3, scale=0.5, **eng)
+    ref = oracle_chain(A, v, 3, 0.5)
+    assert np.linalg.norm(w - ref) <= 3e-13 * np.linalg.norm(ref)
+    w = run(plan, v, precision=nap.PREC_F32, **eng)
+    ref32 = O.spmv_f32(A.row_ptr, A.col, A.val.astype(np.float32), v)
+    assert np.linalg.norm(w - ref32) <= 1e-13 * np.linalg.norm(ref32)
+
+
+def test_strided_partition_engine_limits():
+    """The fused engine cuts SpMV items per node, which a strided partition has
+    no contiguous rows for: fused applies, batches and the no-allocation entry
+    refuse strided plans with ERR_UNSUPPORTED, and the plan stays usable."""
+    A = I.poisson2d(20)
+    plan = gpu_plan(A, 10, 3, nap.F32_VALUES | nap.PARTITION_STRIDED)
+    plan2 = gpu_plan(A, 10, 3, nap.F32_VALUES | nap.PARTITION_STRIDED)
+    vd = torch.from_numpy(I.vector(A.n, 4)).cuda()
+    wd = torch.empty_like(vd)
+    w2 = torch.empty_like(vd)
+    for call in (lambda: nap.napspmv_apply_ex(plan, vd, wd, 1, 1.0,
+                                              nap.make_opts(engine=nap.ENGINE_FUSED)),
+                 lambda: nap.napspmv_apply_batch([plan, plan2], [vd, vd], [wd, w2], [1, 1],
+                                                 [1.0, 1.0]),
+                 lambda: nap.napspmv_apply_noalloc(plan, vd, wd, 1, 1.0)):
+        with pytest.raises(nap.NapError) as e:
+            call()
+        assert e.value.code == nap.ERR_UNSUPPORTED
+    nap.napspmv_apply(plan, vd, wd)
+    assert nap.napspmv_status(plan) == 0
+    v = vd.cpu().numpy()
+    assert_close_fp64(wd.cpu().numpy(), O.spmv(A.row_ptr, A.col, A.val, v), abs_row_bound(A, v))
+
+
 def test_host_entry_point():
     A = I.poisson2d(40)
     v = I.vector(A.n, 4)

@@ -50,6 +50,24 @@ def test_map_text(n_p, ppn):
     assert_plans_equal(gp, O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=O.MAP_TEXT))
 
 
+@pytest.mark.parametrize("n,dens,seed,n_p,ppn", CASES[::2])
+def test_strided_random_patterns(n, dens, seed, n_p, ppn):
+    """Strided partition (row i on process i mod n_p): the same lists, bit for
+    bit, as the oracle's literal evaluation."""
+    A = I.random_pattern(n, dens, seed)
+    gp = gpu_plan(A, n_p, ppn, nap.F32_VALUES | nap.PARTITION_STRIDED)
+    assert_plans_equal(gp, O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=O.STRIDED))
+
+
+@pytest.mark.parametrize("cfg,scale", [(1, 1), (2, 4), (3, 16)])
+def test_strided_workloads(cfg, scale):
+    w = I.workload(cfg, scale)
+    A = w.build()
+    gp = gpu_plan(A, w.n_p, w.ppn, nap.PARTITION_STRIDED | nap.MAP_TEXT)
+    assert_plans_equal(gp, O.OraclePlan(A.row_ptr, A.col, w.n_p, w.ppn,
+                                        flags=O.STRIDED | O.MAP_TEXT))
+
+
 def test_empty_matrix_and_empty_rows():
     n = 50
     A = I.CSR(np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0))
@@ -91,6 +109,9 @@ def test_config3_full_size_counts():
 
 def test_invalid_inputs_rejected():
     A = I.poisson2d(8)
+    with pytest.raises(nap.NapError) as e:
+        nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, 8)  # unknown flag bit
+    assert e.value.code == nap.ERR_ARG
     bad = A.col.copy()
     bad[3] = 64
     with pytest.raises(nap.NapError) as e:
