@@ -43,6 +43,10 @@
  *     P(m)-1-(k mod P(m)), where P(x) is the number of ranks on node x.
  *     Flag ORC_MAP_TEXT sorts the receiving side by |E| descending, as the
  *     prose states.  A node is never split over several processes.
+ *   - Flag ORC_MAP_MAJORITY (the alternative the text names after Eq. U):
+ *     node pair (n,m) is sent by the process of n that owns the most values
+ *     of E(n,m), and received by the process of m whose rows use the most
+ *     of them; ties go to the lowest local process.
  *   - J(on_node -> off_node) from (p,n) to (s,n) is the set of j owned by
  *     (p,n) that appear in some I((s,n),(q,m)); s != p.
  *   - J(off_node -> on_node) from (q,m) to (s,m) is the set of j received
@@ -67,6 +71,7 @@
 
 #define ORC_MAP_TEXT 2 /* same bit as the library's flag, chosen independently */
 #define ORC_STRIDED 4  /* row i belongs to rank i mod n_p (Sec. 5's strided partition) */
+#define ORC_MAP_MAJORITY 8 /* the majority mapping named after Eq. U (see orc_plan_build) */
 
 enum { L_STD = 0, L_NODE, L_INTER, L_J0, L_J1, L_J2, L_BLL, L_BNL, L_LBUF, L_COUNT };
 
@@ -279,6 +284,7 @@ int orc_plan_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t
     int rc = ORC_OK;
     *out = NULL;
     if (np < 1 || np > n || ppn < 1) return ORC_ERR_ARG;
+    if ((flags & ORC_MAP_MAJORITY) && (flags & ORC_MAP_TEXT)) return ORC_ERR_ARG;
     rc = check_csr(n, nnz, row_ptr, col);
     if (rc) return rc;
 
@@ -344,30 +350,57 @@ int orc_plan_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t
             rc = ORC_ERR_OOM;
             goto done;
         }
-        for (int64_t nd = 0; nd < P->nn; nd++) {
-            /* sending side: the nodes of N(nd) */
-            int64_t c = 0;
-            for (int64_t k = 0; k < m; k++)
-                if (N->src[k] == nd) {
-                    e[c].len = N->ptr[k + 1] - N->ptr[k];
-                    e[c].other = N->dst[k];
-                    e[c].msg = k;
-                    c++;
+        if (flags & ORC_MAP_MAJORITY) {
+            /* per node pair, count the values of E(n,m) each process of n owns
+             * and the values each process of m uses, and take the largest */
+            const orc_list *BN = &P->l[L_BNL];
+            for (int64_t k = 0; k < m; k++) {
+                int64_t sn = N->src[k], dn = N->dst[k];
+                int64_t best = -1, arg = 0;
+                for (int64_t p = 0; p < procs_on_node(P, sn); p++) {
+                    int64_t c = 0;
+                    for (int64_t q = N->ptr[k]; q < N->ptr[k + 1]; q++)
+                        if (own(P, N->idx[q]) == sn * ppn + p) c++;
+                    if (c > best) { best = c; arg = p; }
                 }
-            qsort(e, (size_t)c, sizeof(tu_entry), tu_desc);
-            for (int64_t k = 0; k < c; k++) P->send_proc[e[k].msg] = k % procs_on_node(P, nd);
-            /* receiving side: the nodes that have nd in their N(.) */
-            c = 0;
-            for (int64_t k = 0; k < m; k++)
-                if (N->dst[k] == nd) {
-                    e[c].len = N->ptr[k + 1] - N->ptr[k];
-                    e[c].other = N->src[k];
-                    e[c].msg = k;
-                    c++;
+                P->send_proc[k] = arg;
+                best = -1;
+                arg = 0;
+                for (int64_t p = 0; p < procs_on_node(P, dn); p++) {
+                    int64_t c = 0, bs = lrank(BN, dn * ppn + p);
+                    if (bs >= 0)
+                        for (int64_t q = N->ptr[k]; q < N->ptr[k + 1]; q++)
+                            if (lfind(BN, bs, N->idx[q]) >= 0) c++;
+                    if (c > best) { best = c; arg = p; }
                 }
-            qsort(e, (size_t)c, sizeof(tu_entry), (flags & ORC_MAP_TEXT) ? tu_desc : tu_asc);
-            for (int64_t k = 0; k < c; k++)
-                P->recv_proc[e[k].msg] = procs_on_node(P, nd) - 1 - (k % procs_on_node(P, nd));
+                P->recv_proc[k] = arg;
+            }
+        } else {
+            for (int64_t nd = 0; nd < P->nn; nd++) {
+                /* sending side: the nodes of N(nd) */
+                int64_t c = 0;
+                for (int64_t k = 0; k < m; k++)
+                    if (N->src[k] == nd) {
+                        e[c].len = N->ptr[k + 1] - N->ptr[k];
+                        e[c].other = N->dst[k];
+                        e[c].msg = k;
+                        c++;
+                    }
+                qsort(e, (size_t)c, sizeof(tu_entry), tu_desc);
+                for (int64_t k = 0; k < c; k++) P->send_proc[e[k].msg] = k % procs_on_node(P, nd);
+                /* receiving side: the nodes that have nd in their N(.) */
+                c = 0;
+                for (int64_t k = 0; k < m; k++)
+                    if (N->dst[k] == nd) {
+                        e[c].len = N->ptr[k + 1] - N->ptr[k];
+                        e[c].other = N->src[k];
+                        e[c].msg = k;
+                        c++;
+                    }
+                qsort(e, (size_t)c, sizeof(tu_entry), (flags & ORC_MAP_TEXT) ? tu_desc : tu_asc);
+                for (int64_t k = 0; k < c; k++)
+                    P->recv_proc[e[k].msg] = procs_on_node(P, nd) - 1 - (k % procs_on_node(P, nd));
+            }
         }
         free(e);
 

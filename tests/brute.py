@@ -23,7 +23,7 @@ def partition(n, n_p, strided=False):
     return R
 
 
-def brute_plan(n, rows, n_p, ppn, map_text=False, strided=False):
+def brute_plan(n, rows, n_p, ppn, map_text=False, strided=False, majority=False):
     """rows[i] = set of stored columns of row i.  Returns a dict of dicts:
     STD/J0/J1/J2/INTER: {(src, dst): sorted tuple}; NODE: {(n, m): tuple};
     BLL/BNL/LBUF: {rank: tuple}; T, U: {rank: set of nodes}; G: {rank: set};
@@ -62,7 +62,16 @@ def brute_plan(n, rows, n_p, ppn, map_text=False, strided=False):
     # receiving side ascending |E| from the last process, as the tables show)
     T = {r: set() for r in range(n_p)}
     U = {r: set() for r in range(n_p)}
-    for a in range(nn):
+    if majority:
+        # the alternative named after Eq. U: m maps to the process of a that
+        # stores the most of E(a, m); on the receiving side a maps to the
+        # process of m whose rows use the most of E(a, m); ties: lowest process
+        for (a, m), E in NODE.items():
+            own = [len(set(E) & R[r]) for r in node_ranks[a]]
+            T[node_ranks[a][own.index(max(own))]].add(m)
+            use = [len(set(E) & {j for (i, j) in A if i in R[q]}) for q in node_ranks[m]]
+            U[node_ranks[m][use.index(max(use))]].add(a)
+    for a in ([] if majority else range(nn)):
         P = len(node_ranks[a])
         sends = sorted([m for (x, m) in NODE if x == a], key=lambda m: (-len(NODE[(a, m)]), m))
         for k, m in enumerate(sends):

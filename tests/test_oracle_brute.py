@@ -144,3 +144,65 @@ def test_strided_tridiagonal_closed_form(n_p, ppn, k):
     Dc = O.OraclePlan(rp, col, n_p, ppn).list_dict(O.STD)
     assert len(Dc) == 2 * (n_p - 1) and all(len(v) == 1 for v in Dc.values())
 
+
+@pytest.mark.parametrize("n,dens,seed,n_p,ppn", CASES[::3])
+@pytest.mark.parametrize("strided", [False, True])
+def test_majority_mapping_matches_set_definitions(n, dens, seed, n_p, ppn, strided):
+    """The majority mapping (node m to the process storing most of E(n,m), and
+    the receiving process whose rows use most of it), with both partitions."""
+    A = random_pattern(n, dens, seed)
+    flags = O.MAP_MAJORITY | (O.STRIDED if strided else 0)
+    plan = O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=flags)
+    b = brute_plan(n, _rows(A), n_p, ppn, strided=strided, majority=True)
+    for name, kind in LISTS:
+        assert plan.list_dict(kind) == b[name], name
+    for name, kind in LAYOUTS:
+        got = {s: idx for (s, d), idx in plan.list_dict(kind).items()}
+        assert got == b[name], name
+    v = np.random.default_rng(seed).uniform(-1, 1, n)
+    w = plan.napspmv(A.row_ptr, A.col, A.val, v)
+    ref = A.to_dense() @ v
+    assert np.all(np.abs(w - ref) <= 4 * np.finfo(float).eps * (np.abs(A.to_dense()) @ np.abs(v)))
+
+
+def test_majority_mapping_minimises_per_pair_forwarding():
+    """Per node pair, the values of E(n,m) that its sending process does not own
+    (they reach it through the on->off step) and the values its receiving
+    process does not use (they only pass through it) are each the smallest
+    over all processes of the node under the majority mapping: summed over the
+    pairs, never more than under the table mapping.  Inter-node traffic is the
+    same under both."""
+    for seed, (n, n_p, ppn) in enumerate([(48, 12, 4), (60, 10, 5), (45, 9, 3), (80, 20, 4)]):
+        A = random_pattern(n, 0.12, 500 + seed)
+        rows = _rows(A)
+        owner = {}
+        for r in range(n_p):
+            q, rem = divmod(n, n_p)
+            start = r * q + min(r, rem)
+            for i in range(start, start + q + (1 if r < rem else 0)):
+                owner[i] = r
+
+        def forwarded(flags):
+            P = O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=flags)
+            E = P.list_dict(O.NODE)
+            sp, rp = P.tu()
+            keys = sorted(E)
+            not_owned = not_used = 0
+            for k, (a_, m) in enumerate(keys):
+                s_ = a_ * ppn + int(sp[k])
+                q_ = m * ppn + int(rp[k])
+                used = {j for i in range(n) if owner[i] == q_ for j in rows[i]}
+                not_owned += sum(1 for j in E[(a_, m)] if owner[j] != s_)
+                not_used += sum(1 for j in E[(a_, m)] if j not in used)
+            return not_owned, not_used, P.stats()["nap_inter_vals"]
+
+        t_own, t_use, t_inter = forwarded(0)
+        m_own, m_use, m_inter = forwarded(O.MAP_MAJORITY)
+        assert m_own <= t_own and m_use <= t_use and m_inter == t_inter
+
+
+def test_majority_with_map_text_rejected():
+    A = random_pattern(12, 0.3, 1)
+    with pytest.raises(ValueError):
+        O.OraclePlan(A.row_ptr, A.col, 4, 2, flags=O.MAP_MAJORITY | O.MAP_TEXT)
+
