@@ -73,6 +73,13 @@ extern "C" {
  * plan: its applies return ERR_UNSUPPORTED; the phased and overlapped engines
  * serve it. */
 #define NAPSPMV_PARTITION_STRIDED (1u << 2)
+/* Majority mapping, the alternative the text names after Eq. U: node pair
+ * (n,m) is sent by the process of n that owns the most values of E(n,m) and
+ * received by the process of m whose rows use the most of them (ties: the
+ * lowest local process), which minimises per pair the values that reach the
+ * sender through the on->off step and those the receiver only forwards.
+ * Excludes NAPSPMV_MAP_TEXT (ERR_ARG). */
+#define NAPSPMV_MAP_MAJORITY (1u << 3)
 
 /* ------------------------------------------------------------- apply modes */
 #define NAPSPMV_PREC_F64 0 /* FP64 values, FP64 products and sums            */
@@ -172,8 +179,8 @@ typedef struct {
 /* Build the plans of A for n_p simulated processes, ppn per node.
  *   A      CSR (host or device memory), see napspmv_csr.
  *   n_p    1 <= n_p <= N;  ppn >= 1 (the last node may hold fewer processes).
- *   flags  NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT | NAPSPMV_PARTITION_STRIDED;
- *          other bits: ERR_ARG.
+ *   flags  NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT or NAPSPMV_MAP_MAJORITY |
+ *          NAPSPMV_PARTITION_STRIDED; other bits: ERR_ARG.
  *   out    receives the plan; the caller frees it with napspmv_plan_destroy.
  * Runs on the current device and synchronises it.  Errors: ERR_ARG for a
  * malformed CSR or bad n_p / ppn, ERR_UNSUPPORTED beyond the size limits,

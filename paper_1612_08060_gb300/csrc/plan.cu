@@ -463,6 +463,49 @@ struct Cub {
 // A sorted, unique key array (prefix << jb | j) becomes a message list whose
 // prefix is (src << fb | dst); with fb < 0 the prefix is one process id used
 // as both src and dst (the per-process buffer layouts).
+// Majority mapping (the alternative named after Eq. U), sending side: for
+// node pair k (messages of the NODE list, ascending (src, dst)), how many
+// values of E(n,m) each process of n owns.  cnt: [M][ppn].
+__global__ void k_major_send(const int32_t *idx, int64_t total, const int64_t *ptr, int64_t M,
+                             const int32_t *src_node, Part part, int32_t ppn, int32_t *cnt)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = M - 1;  // the pair k with ptr[k] <= e < ptr[k + 1]
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (ptr[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t p = part.owner(idx[e]) - (int64_t)src_node[lo] * ppn;
+        atomicAdd(&cnt[lo * ppn + p], 1);
+    }
+}
+// Receiving side: every (t, j) of the off-node receive sets (key t << jb | j)
+// is a value of E(owner(j)'s node, t's node) that process t's rows use.
+__global__ void k_major_recv(const uint64_t *tj, int64_t n, int jb, const uint64_t *pair_key,
+                             int64_t M, int nb, Part part, int32_t ppn, int32_t *cnt, int *bad)
+{
+    const uint64_t jmask = (1ull << jb) - 1;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = (int64_t)(tj[e] >> jb), j = (int64_t)(tj[e] & jmask);
+        const int64_t sn = part.owner(j) / ppn, dn = t / ppn;
+        const uint64_t key = ((uint64_t)sn << nb) | (uint64_t)dn;
+        int64_t lo = 0, hi = M - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (pair_key[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        if (M == 0 || pair_key[lo] != key) {
+            atomicOr(bad, 64);
+            continue;
+        }
+        atomicAdd(&cnt[lo * ppn + (t - dn * ppn)], 1);
+    }
+}
+
 void make_list(Cub &cb, const uint64_t *keys, int64_t cnt, int fb, int jb, HostList &L)
 {
     L = HostList();
@@ -699,7 +742,44 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
             in_of[ND.dst[k]].push_back(k);
         }
         auto len = [&](int64_t k) { return ND.ptr[k + 1] - ND.ptr[k]; };
-        for (int64_t x = 0; x < nn; x++) {
+        const bool majority = (P->flags & NAPSPMV_MAP_MAJORITY) != 0;
+        if (majority && M > 0) {
+            // per pair: the process of n owning the most of E(n,m) sends, the
+            // process of m whose rows use the most of it receives (ties: lowest)
+            dvec<int32_t> cs(M * ppn), cr(M * ppn);
+            CK(cudaMemset(cs.p, 0, sizeof(int32_t) * M * ppn));
+            CK(cudaMemset(cr.p, 0, sizeof(int32_t) * M * ppn));
+            std::vector<uint64_t> pk(M);
+            for (int64_t k = 0; k < M; k++) pk[k] = ((uint64_t)ND.src[k] << nb) | (uint64_t)ND.dst[k];
+            dvec<int64_t> d_ptr;
+            d_ptr.p = upload(ND.ptr);
+            dvec<int32_t> d_src;
+            d_src.p = upload(ND.src);
+            dvec<uint64_t> d_pk;
+            d_pk.p = upload(pk);
+            k_major_send<<<blocks_for(ND.total), 256>>>(ND.d_idx, ND.total, d_ptr.p, M, d_src.p,
+                                                       part, ppn, cs.p);
+            CK(cudaGetLastError());
+            if (P->n_bnl > 0) {
+                k_major_recv<<<blocks_for(P->n_bnl), 256>>>(bnl_keys.p, P->n_bnl, jb, d_pk.p, M, nb,
+                                                           part, ppn, cr.p, bad.p);
+                CK(cudaGetLastError());
+            }
+            check_bad(bad, "internal: off-node receive value without a node pair");
+            std::vector<int32_t> hs(M * ppn), hr(M * ppn);
+            CK(cudaMemcpy(hs.data(), cs.p, sizeof(int32_t) * M * ppn, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(hr.data(), cr.p, sizeof(int32_t) * M * ppn, cudaMemcpyDeviceToHost));
+            for (int64_t k = 0; k < M; k++) {
+                int64_t bs = 0, br = 0;
+                for (int64_t p = 1; p < procs(ND.src[k]); p++)
+                    if (hs[k * ppn + p] > hs[k * ppn + bs]) bs = p;
+                for (int64_t p = 1; p < procs(ND.dst[k]); p++)
+                    if (hr[k * ppn + p] > hr[k * ppn + br]) br = p;
+                P->send_proc[k] = (int32_t)bs;
+                P->recv_proc[k] = (int32_t)br;
+            }
+        }
+        for (int64_t x = 0; x < (majority ? 0 : nn); x++) {
             auto &o = out_of[x];
             std::stable_sort(o.begin(), o.end(), [&](int64_t a, int64_t b) {
                 if (len(a) != len(b)) return len(a) > len(b);
@@ -998,8 +1078,13 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         set_error(NAPSPMV_ERR_ARG, "need 1 <= n_p <= N and ppn >= 1");
         return NAPSPMV_ERR_ARG;
     }
-    if (flags & ~(NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT | NAPSPMV_PARTITION_STRIDED)) {
+    if (flags & ~(NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT | NAPSPMV_PARTITION_STRIDED |
+                  NAPSPMV_MAP_MAJORITY)) {
         set_error(NAPSPMV_ERR_ARG, "unknown plan flag");
+        return NAPSPMV_ERR_ARG;
+    }
+    if ((flags & NAPSPMV_MAP_MAJORITY) && (flags & NAPSPMV_MAP_TEXT)) {
+        set_error(NAPSPMV_ERR_ARG, "NAPSPMV_MAP_MAJORITY and NAPSPMV_MAP_TEXT exclude each other");
         return NAPSPMV_ERR_ARG;
     }
     if (A->n >= (1ll << 30) || A->nnz >= (1ll << 31) - 64) {

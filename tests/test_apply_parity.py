@@ -182,6 +182,16 @@ def test_strided_partition(eng, n, dens, n_p, ppn):
     assert np.linalg.norm(w - ref32) <= 1e-13 * np.linalg.norm(ref32)
 
 
+@pytest.mark.parametrize("eng", ENGINES)
+def test_majority_mapping_apply(eng):
+    A = I.random_pattern(400, 0.02, 31)
+    v = I.vector(400, 32)
+    plan = gpu_plan(A, 40, 4, nap.F32_VALUES | nap.MAP_MAJORITY)
+    w = run(plan, v, reps=2, scale=0.5, **eng)
+    ref = oracle_chain(A, v, 2, 0.5)
+    assert np.linalg.norm(w - ref) <= 2e-13 * np.linalg.norm(ref)
+
+
 def test_strided_partition_engine_limits():
     """The fused engine cuts SpMV items per node, which a strided partition has
     no contiguous rows for: fused applies, batches and the no-allocation entry

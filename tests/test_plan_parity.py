@@ -68,6 +68,26 @@ def test_strided_workloads(cfg, scale):
                                         flags=O.STRIDED | O.MAP_TEXT))
 
 
+@pytest.mark.parametrize("n,dens,seed,n_p,ppn", CASES[1::3])
+@pytest.mark.parametrize("strided", [False, True])
+def test_majority_mapping(n, dens, seed, n_p, ppn, strided):
+    """The majority mapping of node pairs (NAPSPMV_MAP_MAJORITY), both
+    partitions: bit-exact against the oracle."""
+    A = I.random_pattern(n, dens, seed)
+    gflags = nap.MAP_MAJORITY | (nap.PARTITION_STRIDED if strided else 0)
+    oflags = O.MAP_MAJORITY | (O.STRIDED if strided else 0)
+    assert_plans_equal(gpu_plan(A, n_p, ppn, gflags),
+                       O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=oflags))
+
+
+@pytest.mark.parametrize("cfg,scale", [(1, 1), (2, 4), (4, 64)])
+def test_majority_mapping_workloads(cfg, scale):
+    w = I.workload(cfg, scale)
+    A = w.build()
+    assert_plans_equal(gpu_plan(A, w.n_p, w.ppn, nap.MAP_MAJORITY),
+                       O.OraclePlan(A.row_ptr, A.col, w.n_p, w.ppn, flags=O.MAP_MAJORITY))
+
+
 def test_empty_matrix_and_empty_rows():
     n = 50
     A = I.CSR(np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0))
@@ -110,7 +130,10 @@ def test_config3_full_size_counts():
 def test_invalid_inputs_rejected():
     A = I.poisson2d(8)
     with pytest.raises(nap.NapError) as e:
-        nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, 8)  # unknown flag bit
+        nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, 16)  # unknown flag bit
+    assert e.value.code == nap.ERR_ARG
+    with pytest.raises(nap.NapError) as e:
+        nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, nap.MAP_MAJORITY | nap.MAP_TEXT)
     assert e.value.code == nap.ERR_ARG
     bad = A.col.copy()
     bad[3] = 64
