@@ -170,9 +170,10 @@ def run_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name + ("_strided" if args.partition == "strided" else ""),
+        "config": {"workload": w.name + ("_strided" if args.partition == "strided" else "") + (
+                       "_composed" if args.gathers == "composed" else ""),
                    "n": A.n, "nnz": A.nnz, "n_p": w.n_p, "ppn": w.ppn,
-                   "partition": args.partition,
+                   "partition": args.partition, "gathers": args.gathers,
                    "applies_per_step": 1},
         "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} plain FP64 CSR SpMVs of the full matrix, "
@@ -239,6 +240,9 @@ def main():
     ap.add_argument("--tile-nnz", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--pipeline", default="default", choices=["default", "cta", "warp"])
+    ap.add_argument("--gathers", default="literal", choices=["literal", "composed"],
+                    help="composed: receive buffers gathered straight from v (an ablation "
+                         "of the node-aware exchange's hops)")
     ap.add_argument("--partition", default="contiguous", choices=["contiguous", "strided"],
                     help="strided: row i on process i mod n_p (the SuiteSparse runs' partition)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
@@ -274,7 +278,8 @@ def main():
     torch.cuda.set_device(dev)
     w, A, v = build_workload(args.config)
     t0 = time.perf_counter()
-    pflags = nap.F32_VALUES | (nap.PARTITION_STRIDED if args.partition == "strided" else 0)
+    pflags = nap.F32_VALUES | (nap.PARTITION_STRIDED if args.partition == "strided" else 0) | (
+        nap.COMPOSED_GATHERS if args.gathers == "composed" else 0)
     plan = nap.napspmv_plan(A.row_ptr, A.col, A.val, w.n_p, w.ppn, pflags)
     plan_ms = (time.perf_counter() - t0) * 1e3
     st = nap.napspmv_plan_stats(plan)
@@ -286,7 +291,12 @@ def main():
     # message steps: 4 B read + 4 B write + 4 B index per element and hop
     # instead of 8 + 8 + 4 (the fused engine keeps FP64 messages)
     f32_msgs = f32 and args.engine != "fused"
-    if f32_msgs:
+    if args.gathers == "composed":
+        # two gathers from v: 8 B read + 8 B write + 4 B index per value
+        B = B_csr + 20.0 * (st["bll_total"] + st["bnl_total"])
+        if f32:
+            B -= 8.0 * (st["bll_total"] + st["bnl_total"])
+    elif f32_msgs:
         B -= st["bytes_msg"] * 8.0 / 20.0
     # SpMV step alone: row pointer, column + value streams, each x and each
     # received value read once, w written once; in FP32 mode the step also
@@ -406,9 +416,10 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32-values/f64-sums" if f32 else "f64", "data": "synthetic",
-        "config": {"workload": w.name + ("_strided" if args.partition == "strided" else ""),
+        "config": {"workload": w.name + ("_strided" if args.partition == "strided" else "") + (
+                       "_composed" if args.gathers == "composed" else ""),
                    "n": A.n, "nnz": A.nnz, "n_p": w.n_p, "ppn": w.ppn,
-                   "partition": args.partition,
+                   "partition": args.partition, "gathers": args.gathers,
                    "applies_per_step": args.reps, "scale": SCALE,
                    "engine": {1: "fused", 2: "phased", 3: "overlap"}[opts.engine or eff.engine],
                    "vec": opts.vec or eff.vec, "chunk": opts.chunk or eff.chunk,

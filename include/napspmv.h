@@ -80,6 +80,14 @@ extern "C" {
  * sender through the on->off step and those the receiver only forwards.
  * Excludes NAPSPMV_MAP_TEXT (ERR_ARG). */
 #define NAPSPMV_MAP_MAJORITY (1u << 3)
+/* Composed gathers, an ablation with no counterpart in the paper: each
+ * process's receive buffers are gathered straight from v (b_{l->l} as in the
+ * on->on step, b_{nl->l} from the owners' values), skipping the on->off
+ * gather, pack, transfer and off->on hops of Algorithm NAPSpMV.  The plan and
+ * its statistics are unchanged; the result has the same bits as the literal
+ * exchange.  Phased and overlapped engines only (the fused engine, batches
+ * and the no-allocation entry give ERR_UNSUPPORTED). */
+#define NAPSPMV_COMPOSED_GATHERS (1u << 4)
 
 /* ------------------------------------------------------------- apply modes */
 #define NAPSPMV_PREC_F64 0 /* FP64 values, FP64 products and sums            */
@@ -180,7 +188,8 @@ typedef struct {
  *   A      CSR (host or device memory), see napspmv_csr.
  *   n_p    1 <= n_p <= N;  ppn >= 1 (the last node may hold fewer processes).
  *   flags  NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT or NAPSPMV_MAP_MAJORITY |
- *          NAPSPMV_PARTITION_STRIDED; other bits: ERR_ARG.
+ *          NAPSPMV_PARTITION_STRIDED | NAPSPMV_COMPOSED_GATHERS; other bits:
+ *          ERR_ARG.
  *   out    receives the plan; the caller frees it with napspmv_plan_destroy.
  * Runs on the current device and synchronises it.  Errors: ERR_ARG for a
  * malformed CSR or bad n_p / ppn, ERR_UNSUPPORTED beyond the size limits,

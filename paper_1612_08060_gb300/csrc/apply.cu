@@ -1507,6 +1507,28 @@ static int64_t enqueue_messages(const napspmv_plan_t *P, const T *x, T *bll, T *
     return nk;
 }
 
+// Composed gathers (plan flag NAPSPMV_COMPOSED_GATHERS): both receive buffers
+// straight from x with the on->on and off-node receive index lists, one
+// kernel; the hops of the node-aware exchange are skipped.
+static int64_t enqueue_composed(const napspmv_plan_t *P, const void *x, napspmv_ws_t *ws, bool f32,
+                                cudaStream_t s)
+{
+    const int64_t n = P->n_bll + P->n_bnl;
+    if (n == 0) return 0;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
+                                                              (int64_t)P->num_sms * 8));
+    if (f32)
+        k_gather2<float><<<g, NT, 0, s>>>(
+            static_cast<const float *>(x), P->lists[L_BLL].d_idx,
+            reinterpret_cast<float *>(ws->bll), (int)P->n_bll, P->lists[L_BNL].d_idx,
+            reinterpret_cast<float *>(ws->bnl), (int)P->n_bnl, ws->err);
+    else
+        k_gather2<double><<<g, NT, 0, s>>>(static_cast<const double *>(x), P->lists[L_BLL].d_idx,
+                                           ws->bll, (int)P->n_bll, P->lists[L_BNL].d_idx, ws->bnl,
+                                           (int)P->n_bnl, ws->err);
+    return 1;
+}
+
 static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
                           double scale, const napspmv_opts &o, cudaStream_t s, int64_t *kernels)
 {
@@ -1547,7 +1569,9 @@ static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, 
             nk++;
             NAP_CUDA(cudaEventRecord(P->ev_join, P->aux));
         }
-        if (f32)
+        if (P->flags & NAPSPMV_COMPOSED_GATHERS)
+            nk += enqueue_composed(P, f32 ? (const void *)x32 : (const void *)x, ws, f32, s);
+        else if (f32)
             nk += enqueue_messages<float>(P, x32, reinterpret_cast<float *>(ws->bll),
                                           reinterpret_cast<float *>(ws->lbuf),
                                           reinterpret_cast<float *>(ws->gsend),
@@ -1651,6 +1675,11 @@ static int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
                                            "strided plan runs on the phased or overlapped engine");
         return NAPSPMV_ERR_UNSUPPORTED;
     }
+    if (o.engine == NAPSPMV_ENGINE_FUSED && (P->flags & NAPSPMV_COMPOSED_GATHERS)) {
+        set_error(NAPSPMV_ERR_UNSUPPORTED, "composed gathers run on the phased or overlapped "
+                                           "engine only");
+        return NAPSPMV_ERR_UNSUPPORTED;
+    }
     if (o.timeout_ms < 1) {
         set_error(NAPSPMV_ERR_ARG, "timeout_ms must be >= 1");
         return NAPSPMV_ERR_ARG;
@@ -1698,9 +1727,10 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
             rc = NAPSPMV_ERR_ARG;
             break;
         }
-        if (count > 1 && (P->flags & NAPSPMV_PARTITION_STRIDED)) {
-            set_error(NAPSPMV_ERR_UNSUPPORTED, "batched applies run the fused engine, which "
-                                               "needs contiguous node rows (no strided plans)");
+        if (count > 1 && (P->flags & (NAPSPMV_PARTITION_STRIDED | NAPSPMV_COMPOSED_GATHERS))) {
+            set_error(NAPSPMV_ERR_UNSUPPORTED,
+                      "batched applies run the fused engine, which needs contiguous node rows "
+                      "and literal exchanges (no strided or composed-gather plans)");
             rc = NAPSPMV_ERR_UNSUPPORTED;
             break;
         }
@@ -1764,9 +1794,9 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
         set_error(NAPSPMV_ERR_ARG, "NULL plan or vector, reps < 1, or w == v");
         return NAPSPMV_ERR_ARG;
     }
-    if (P->flags & NAPSPMV_PARTITION_STRIDED) {
+    if (P->flags & (NAPSPMV_PARTITION_STRIDED | NAPSPMV_COMPOSED_GATHERS)) {
         set_error(NAPSPMV_ERR_UNSUPPORTED, "napspmv_apply_noalloc runs the fused engine, which "
-                                           "needs contiguous node rows (no strided plans)");
+                                           "needs contiguous node rows and literal exchanges");
         return NAPSPMV_ERR_UNSUPPORTED;
     }
     // doubles of scratch: counters (as 8-byte words), b_{l->l}, b_{l->nl},

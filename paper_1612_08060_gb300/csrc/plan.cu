@@ -1079,7 +1079,7 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         return NAPSPMV_ERR_ARG;
     }
     if (flags & ~(NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT | NAPSPMV_PARTITION_STRIDED |
-                  NAPSPMV_MAP_MAJORITY)) {
+                  NAPSPMV_MAP_MAJORITY | NAPSPMV_COMPOSED_GATHERS)) {
         set_error(NAPSPMV_ERR_ARG, "unknown plan flag");
         return NAPSPMV_ERR_ARG;
     }

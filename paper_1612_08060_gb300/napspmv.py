@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libnapspmv.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 HOST, DEVICE = 0, 1
-F32_VALUES, MAP_TEXT, PARTITION_STRIDED, MAP_MAJORITY = 1, 2, 4, 8
+F32_VALUES, MAP_TEXT, PARTITION_STRIDED, MAP_MAJORITY, COMPOSED_GATHERS = 1, 2, 4, 8, 16
 PREC_F64, PREC_F32 = 0, 1
 ENGINE_DEFAULT, ENGINE_FUSED, ENGINE_PHASED, ENGINE_OVERLAP = 0, 1, 2, 3
 PIPELINE_CTA, PIPELINE_WARP = 1, 2

@@ -192,6 +192,44 @@ def test_majority_mapping_apply(eng):
     assert np.linalg.norm(w - ref) <= 2e-13 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("strided", [False, True])
+@pytest.mark.parametrize("prec", [nap.PREC_F64, nap.PREC_F32])
+def test_composed_gathers_same_bits(strided, prec):
+    """Composed gathers fetch each receive buffer straight from v; the literal
+    exchange delivers the same values through its hops, so every phased
+    engine gives identical bits with either plan."""
+    A = I.random_pattern(600, 0.015, 41)
+    v = I.vector(600, 42)
+    part = nap.PARTITION_STRIDED if strided else 0
+    lit = gpu_plan(A, 48, 4, nap.F32_VALUES | part)
+    com = gpu_plan(A, 48, 4, nap.F32_VALUES | part | nap.COMPOSED_GATHERS)
+    for eng in [e for e in ENGINES if e["engine"] != nap.ENGINE_FUSED]:
+        for reps in (1, 3):
+            a = run(lit, v, reps=reps, scale=0.5, precision=prec, **eng)
+            b = run(com, v, reps=reps, scale=0.5, precision=prec, **eng)
+            assert np.array_equal(a, b), (eng, reps)
+    ref = oracle_chain(A, v, 3, 0.5)
+    if prec == nap.PREC_F64:
+        assert np.linalg.norm(b - ref) <= 3e-13 * np.linalg.norm(ref)
+
+
+def test_composed_gathers_engine_limits():
+    A = I.poisson2d(16)
+    plan = gpu_plan(A, 8, 2, nap.F32_VALUES | nap.COMPOSED_GATHERS)
+    plan2 = gpu_plan(A, 8, 2, nap.F32_VALUES | nap.COMPOSED_GATHERS)
+    vd = torch.from_numpy(I.vector(A.n, 5)).cuda()
+    wd = torch.empty_like(vd)
+    w2 = torch.empty_like(vd)
+    for call in (lambda: nap.napspmv_apply_ex(plan, vd, wd, 1, 1.0,
+                                              nap.make_opts(engine=nap.ENGINE_FUSED)),
+                 lambda: nap.napspmv_apply_batch([plan, plan2], [vd, vd], [wd, w2], [1, 1],
+                                                 [1.0, 1.0]),
+                 lambda: nap.napspmv_apply_noalloc(plan, vd, wd, 1, 1.0)):
+        with pytest.raises(nap.NapError) as e:
+            call()
+        assert e.value.code == nap.ERR_UNSUPPORTED
+
+
 def test_strided_partition_engine_limits():
     """The fused engine cuts SpMV items per node, which a strided partition has
     no contiguous rows for: fused applies, batches and the no-allocation entry

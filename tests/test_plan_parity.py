@@ -130,7 +130,7 @@ def test_config3_full_size_counts():
 def test_invalid_inputs_rejected():
     A = I.poisson2d(8)
     with pytest.raises(nap.NapError) as e:
-        nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, 16)  # unknown flag bit
+        nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, 32)  # unknown flag bit
     assert e.value.code == nap.ERR_ARG
     with pytest.raises(nap.NapError) as e:
         nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, nap.MAP_MAJORITY | nap.MAP_TEXT)
