@@ -308,6 +308,9 @@ def main():
                     help="also compare continuous batching with the plain loop on this many "
                          "requests of the serving mix")
     ap.add_argument("--serve-nmax", type=float, default=2e5)
+    ap.add_argument("--serve-sweep", default="",
+                    help="comma-separated further loads (fractions of the plain loop's "
+                         "saturated throughput), e.g. 0.5,1.0,1.2")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
                     help="f32: FP32-stored values, FP32 products, FP64 sums")
     ap.add_argument("--profile-spmv", type=int, default=0,
@@ -510,7 +513,8 @@ def main():
         line["cpu_baseline"] = cpu_baseline_leg(A, v, w_one, B, args.cpu_budget)
     if args.serve > 0 and ws == 1:
         from paper_1612_08060_gb300 import serve
-        line["serving"] = serve.compare(args.serve, n_hi=args.serve_nmax, device=dev)
+        sweep = tuple(float(x) for x in args.serve_sweep.split(",") if x.strip())
+        line["serving"] = serve.compare(args.serve, n_hi=args.serve_nmax, device=dev, sweep=sweep)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

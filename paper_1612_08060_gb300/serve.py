@@ -264,30 +264,40 @@ def warm_cache(specs, device=None):
     return srv.cache, time.perf_counter() - t0
 
 
-def compare(count=512, n_lo=1e3, n_hi=2e5, seed=1239, load=0.8, device=None):
+def compare(count=512, n_lo=1e3, n_hi=2e5, seed=1239, load=0.8, device=None, sweep=()):
     """Continuous batching vs the plain per-request loop on the same requests.
 
     The plain loop's saturated throughput (all requests queued at once) sets the
     arrival rate lambda = load * throughput; both loops then serve the same
-    Poisson arrivals in real time.  Plans are built beforehand and shared."""
+    Poisson arrivals in real time.  Plans are built beforehand and shared.
+    `sweep`: further loads, each reported under "sweep" the same way."""
     base = inputs.serving_requests(count, 1.0, seed, n_lo=n_lo, n_hi=n_hi)
     cache, build_s = warm_cache(base, device)
     t0 = time.perf_counter()
     plain_sat = Server(max_active=1, cache=cache, device=device).run(base, realtime=False)
     sat_s = time.perf_counter() - t0
-    rate = load * count / sat_s
-    specs = inputs.serving_requests(count, rate, seed, n_lo=n_lo, n_hi=n_hi)
-    out = {"requests": count, "n_range": [n_lo, n_hi], "rate_hz": rate,
-           "plan_build_s": build_s, "plain_saturated_rps": count / sat_s,
-           "mix": {"spmv": sum(r["kind"] == "spmv" for r in specs),
-                   "cg": sum(r["kind"] == "cg" for r in specs)},
-           "tolerance": "SpMV FP64 <= 1e-13 normwise; CG-IR ||b - Ax|| / ||b|| <= 1e-10"}
-    for name, act in (("batched", 64), ("plain", 1)):
-        srv = Server(max_active=act, cache=cache, device=device)
-        t0 = time.perf_counter()
-        reqs = srv.run(specs, realtime=True)
-        wall = time.perf_counter() - t0
-        out[name] = summarize(reqs, wall)
-        out[name]["mean_batch"] = float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0
+
+    def at(ld):
+        rate = ld * count / sat_s
+        specs = inputs.serving_requests(count, rate, seed, n_lo=n_lo, n_hi=n_hi)
+        res = {"load": ld, "rate_hz": rate,
+               "mix": {"spmv": sum(r["kind"] == "spmv" for r in specs),
+                       "cg": sum(r["kind"] == "cg" for r in specs)}}
+        for name, act in (("batched", 64), ("plain", 1)):
+            srv = Server(max_active=act, cache=cache, device=device)
+            t1 = time.perf_counter()
+            reqs = srv.run(specs, realtime=True)
+            wall = time.perf_counter() - t1
+            res[name] = summarize(reqs, wall)
+            res[name]["mean_batch"] = float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0
+        return res
+
+    main = at(load)
+    out = {"requests": count, "n_range": [n_lo, n_hi], "rate_hz": main["rate_hz"],
+           "plan_build_s": build_s, "plain_saturated_rps": count / sat_s, "mix": main["mix"],
+           "tolerance": "SpMV FP64 <= 1e-13 normwise; CG-IR ||b - Ax|| / ||b|| <= 1e-10",
+           "batched": main["batched"], "plain": main["plain"]}
+    if sweep:
+        out["sweep"] = [at(ld) for ld in sweep]
     del plain_sat
     return out
