@@ -117,6 +117,22 @@ __device__ __forceinline__ uint32_t ld_stream_hint_u32(const uint32_t *p, uint64
     return v;
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with the
+// programmatic-serialization attribute may become resident while its
+// predecessor in the stream drains: griddep_wait() waits, in hardware, until
+// the predecessor grid has completed and its writes are visible, and
+// griddep_done(), called when a CTA has issued its last work, lets the
+// dependent grid start as this grid's CTAs finish (a CTA that exits early
+// counts as done).  Without a programmatic predecessor both are no-ops.
+__device__ __forceinline__ void griddep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_done()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ long long globaltimer()
 {
     long long t;
@@ -821,6 +837,7 @@ __global__ void __launch_bounds__(NT)
     k_gather2(const T *x, const int32_t *bll_j, T *bll, int n_bll, const int32_t *lbuf_j, T *lbuf,
               int n_lbuf, const int *err)
 {
+    griddep_wait();
     if (*(volatile const int *)err) return;  // sticky error: no work until cleared
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n_bll + n_lbuf; b += gridDim.x * per) {
@@ -831,40 +848,49 @@ __global__ void __launch_bounds__(NT)
             step_gather<false, 8, T>(lbuf, x, lbuf_j, lb, le, threadIdx.x);
         }
     }
+    griddep_done();
 }
 template <class T>
 __global__ void __launch_bounds__(NT)
     k_pack(const T *x, const T *lbuf, const uint32_t *src, T *gsend, int n, const int *err)
 {
+    griddep_wait();
     if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
         step_pack<false, 8, T>(gsend, x, lbuf, src, b, min(b + per, n), threadIdx.x);
+    griddep_done();
 }
 template <class T>
 __global__ void __launch_bounds__(NT)
     k_transfer(const T *gsend, const int32_t *dst, T *grecv, int n, const int *err)
 {
+    griddep_wait();
     if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
         step_transfer<false, 8, T>(grecv, gsend, dst, b, min(b + per, n), threadIdx.x);
+    griddep_done();
 }
 template <class T>
 __global__ void __launch_bounds__(NT)
     k_unpack(const T *grecv, const int32_t *src, T *bnl, int n, const int *err)
 {
+    griddep_wait();
     if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
         step_gather<false, 8, T>(bnl, grecv, src, b, min(b + per, n), threadIdx.x);
+    griddep_done();
 }
 // FP32 copy of an input vector (first apply of a chain in FP32 mode)
 __global__ void __launch_bounds__(NT) k_to_f32(const double *v, float *v32, int64_t n, const int *err)
 {
+    griddep_wait();
     if (*(volatile const int *)err) return;
     for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
         v32[i] = __double2float_rn(ld_stream_f64(v + i));
+    griddep_done();
 }
 template <int V, bool F32, int MODE = kFull>
 __global__ void __launch_bounds__(NT)
@@ -877,6 +903,7 @@ __global__ void __launch_bounds__(NT)
              *bnl = static_cast<const XT *>(bnls);
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
+    griddep_wait();
     if (*(volatile const int *)err) return;  // sticky error: no work until cleared
     constexpr int VB = F32 ? 4 : 8;
     tile_smem_init(smem, ns);
@@ -919,6 +946,7 @@ __global__ void __launch_bounds__(NT)
         cur = cur + 1 == ns ? 0 : cur + 1;
         __syncthreads();
     }
+    griddep_done();
 }
 
 // ----------------------------------------------- warp-pipelined SpMV
@@ -944,6 +972,7 @@ __global__ void __launch_bounds__(NT)
     const XT *x = static_cast<const XT *>(xs), *bll = static_cast<const XT *>(blls),
              *bnl = static_cast<const XT *>(bnls);
     extern __shared__ __align__(16) unsigned char smem[];
+    griddep_wait();
     if (*(volatile const int *)err) return;  // sticky error: no work until cleared
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const StageLayout L = stage_layout(capw, rowsw, F32 ? 4 : 8);
@@ -1047,6 +1076,7 @@ __global__ void __launch_bounds__(NT)
         cur = cur + 1 == ns ? 0 : cur + 1;
         __syncwarp();
     }
+    griddep_done();
 }
 
 // ------------------------------------------------------------- dispatch
@@ -1468,21 +1498,43 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
         L.grid = std::max(1, std::min(ctas, P->num_sms * std::max(occ - 1, 1)));
     return NAPSPMV_OK;
 }
+// Launch with programmatic stream serialization: the kernel may become
+// resident while its stream predecessor drains (it waits in griddep_enter).
+// Errors surface through cudaGetLastError like a <<<>>> launch.
+// pdl = false: an ordinary launch.
+template <typename... KArgs, typename... Args>
+static void launch_pdl(bool pdl, void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t s,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    (void)cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // x: the apply's input (FP64), or its FP32 copy in FP32 mode, where the
 // receive buffers hold FP32 copies too; y32 (FP32 mode, may be null) receives
 // the finished rows rounded to FP32.
 static void spmv_run(const SpmvLaunch &L, const void *x, const napspmv_ws_t *ws, double *y,
-                     float *y32, double scale, int stages, cudaStream_t s)
+                     float *y32, double scale, int stages, cudaStream_t s, bool pdl)
 {
-    L.fn<<<L.grid, NT, L.sm, s>>>(L.A, x, ws->bll, ws->bnl, y, y32, make_scale(scale), L.tiles,
-                                  L.n, L.cap, L.rows, stages, ws->err);
+    launch_pdl(pdl, L.fn, L.grid, L.sm, s, L.A, x, (const void *)ws->bll, (const void *)ws->bnl, y, y32,
+               make_scale(scale), L.tiles, L.n, L.cap, L.rows, stages, ws->err);
 }
 
 // The four message steps of one apply (phases 1-4) as kernels on stream s;
-// returns the number of launches.
+// returns the number of launches.  The later steps are launched as
+// programmatic dependents of the earlier ones; pdl_first: the first step too.
 template <class T>
 static int64_t enqueue_messages(const napspmv_plan_t *P, const T *x, T *bll, T *lbuf, T *gsend,
-                                T *grecv, T *bnl, int *err, cudaStream_t s)
+                                T *grecv, T *bnl, int *err, cudaStream_t s, bool pdl_first)
 {
     auto grid = [&](int64_t n) {
         return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
@@ -1490,18 +1542,22 @@ static int64_t enqueue_messages(const napspmv_plan_t *P, const T *x, T *bll, T *
     };
     int64_t nk = 0;
     if (P->n_bll + P->n_lbuf > 0) {
-        k_gather2<T><<<grid(P->n_bll + P->n_lbuf), NT, 0, s>>>(
-            x, P->lists[L_BLL].d_idx, bll, (int)P->n_bll, P->lists[L_LBUF].d_idx, lbuf,
-            (int)P->n_lbuf, err);
+        launch_pdl(pdl_first, k_gather2<T>, grid(P->n_bll + P->n_lbuf), 0, s, x,
+                   (const int32_t *)P->lists[L_BLL].d_idx, bll, (int)P->n_bll,
+                   (const int32_t *)P->lists[L_LBUF].d_idx, lbuf, (int)P->n_lbuf,
+                   (const int *)err);
         nk++;
     }
     if (P->n_gs > 0) {
-        k_pack<T><<<grid(P->n_gs), NT, 0, s>>>(x, lbuf, P->d_pack_src, gsend, (int)P->n_gs, err);
-        k_transfer<T><<<grid(P->n_gs), NT, 0, s>>>(gsend, P->d_xfer_dst, grecv, (int)P->n_gs, err);
+        launch_pdl(true, k_pack<T>, grid(P->n_gs), 0, s, x, (const T *)lbuf,
+                   (const uint32_t *)P->d_pack_src, gsend, (int)P->n_gs, (const int *)err);
+        launch_pdl(true, k_transfer<T>, grid(P->n_gs), 0, s, (const T *)gsend,
+                   (const int32_t *)P->d_xfer_dst, grecv, (int)P->n_gs, (const int *)err);
         nk += 2;
     }
     if (P->n_bnl > 0) {
-        k_unpack<T><<<grid(P->n_bnl), NT, 0, s>>>(grecv, P->d_unp_src, bnl, (int)P->n_bnl, err);
+        launch_pdl(true, k_unpack<T>, grid(P->n_bnl), 0, s, (const T *)grecv,
+                   (const int32_t *)P->d_unp_src, bnl, (int)P->n_bnl, (const int *)err);
         nk++;
     }
     return nk;
@@ -1511,21 +1567,22 @@ static int64_t enqueue_messages(const napspmv_plan_t *P, const T *x, T *bll, T *
 // straight from x with the on->on and off-node receive index lists, one
 // kernel; the hops of the node-aware exchange are skipped.
 static int64_t enqueue_composed(const napspmv_plan_t *P, const void *x, napspmv_ws_t *ws, bool f32,
-                                cudaStream_t s)
+                                cudaStream_t s, bool pdl)
 {
     const int64_t n = P->n_bll + P->n_bnl;
     if (n == 0) return 0;
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
                                                               (int64_t)P->num_sms * 8));
     if (f32)
-        k_gather2<float><<<g, NT, 0, s>>>(
-            static_cast<const float *>(x), P->lists[L_BLL].d_idx,
-            reinterpret_cast<float *>(ws->bll), (int)P->n_bll, P->lists[L_BNL].d_idx,
-            reinterpret_cast<float *>(ws->bnl), (int)P->n_bnl, ws->err);
+        launch_pdl(pdl, k_gather2<float>, g, 0, s, static_cast<const float *>(x),
+                   (const int32_t *)P->lists[L_BLL].d_idx, reinterpret_cast<float *>(ws->bll),
+                   (int)P->n_bll, (const int32_t *)P->lists[L_BNL].d_idx,
+                   reinterpret_cast<float *>(ws->bnl), (int)P->n_bnl, (const int *)ws->err);
     else
-        k_gather2<double><<<g, NT, 0, s>>>(static_cast<const double *>(x), P->lists[L_BLL].d_idx,
-                                           ws->bll, (int)P->n_bll, P->lists[L_BNL].d_idx, ws->bnl,
-                                           (int)P->n_bnl, ws->err);
+        launch_pdl(pdl, k_gather2<double>, g, 0, s, static_cast<const double *>(x),
+                   (const int32_t *)P->lists[L_BLL].d_idx, ws->bll, (int)P->n_bll,
+                   (const int32_t *)P->lists[L_BNL].d_idx, ws->bnl, (int)P->n_bnl,
+                   (const int *)ws->err);
     return 1;
 }
 
@@ -1550,7 +1607,8 @@ static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, 
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
     int64_t nk = 0;
     if (f32) {
-        k_to_f32<<<grid(P->n), NT, 0, s>>>(v, ws->x32[0], P->n, ws->err);
+        launch_pdl(!overlap, k_to_f32, grid(P->n), 0, s, v, ws->x32[0], (int64_t)P->n,
+                   (const int *)ws->err);
         nk++;
     }
     ws->buf_f32 = f32 ? 1 : 0;
@@ -1565,26 +1623,31 @@ static int enqueue_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, 
             // runs on a second stream while the message steps proceed
             NAP_CUDA(cudaEventRecord(P->ev_fork, s));
             NAP_CUDA(cudaStreamWaitEvent(P->aux, P->ev_fork, 0));
-            spmv_run(LL, xs, ws, y, nullptr, scale, o.stages, P->aux);
+            spmv_run(LL, xs, ws, y, nullptr, scale, o.stages, P->aux, false);
             nk++;
             NAP_CUDA(cudaEventRecord(P->ev_join, P->aux));
         }
+        // programmatic dependent launches: every edge of the phased engine; in
+        // the overlapped engine only inside the message chain, where the local
+        // pass is already resident (an early-resident first step or remote
+        // pass would hold the slots the local pass needs)
+        const bool pdl = !overlap;
         if (P->flags & NAPSPMV_COMPOSED_GATHERS)
-            nk += enqueue_composed(P, f32 ? (const void *)x32 : (const void *)x, ws, f32, s);
+            nk += enqueue_composed(P, f32 ? (const void *)x32 : (const void *)x, ws, f32, s, pdl);
         else if (f32)
             nk += enqueue_messages<float>(P, x32, reinterpret_cast<float *>(ws->bll),
                                           reinterpret_cast<float *>(ws->lbuf),
                                           reinterpret_cast<float *>(ws->gsend),
                                           reinterpret_cast<float *>(ws->grecv),
-                                          reinterpret_cast<float *>(ws->bnl), ws->err, s);
+                                          reinterpret_cast<float *>(ws->bnl), ws->err, s, pdl);
         else
             nk += enqueue_messages<double>(P, x, ws->bll, ws->lbuf, ws->gsend, ws->grecv, ws->bnl,
-                                           ws->err, s);
+                                           ws->err, s, pdl);
         if (overlap) {
             NAP_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
-            spmv_run(LR, xs, ws, y, y32, scale, o.stages, s);
+            spmv_run(LR, xs, ws, y, y32, scale, o.stages, s, false);
         } else {
-            spmv_run(LF, xs, ws, y, y32, scale, o.stages, s);
+            spmv_run(LF, xs, ws, y, y32, scale, o.stages, s, true);
         }
         nk++;
         NAP_CUDA(cudaGetLastError());
@@ -1891,6 +1954,8 @@ extern "C" int napspmv_spmv_step(napspmv_plan_t *P, napspmv_ws_t *ws, const doub
     if (cur != P->device) NAP_CUDA(cudaSetDevice(P->device));
     if ((rc = build_items(P, o.chunk, o.tile_rows, o.tile_nnz))) return rc;
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
+    // launched as the phased engine launches its SpMV pass
+    const bool pdl = o.engine == NAPSPMV_ENGINE_PHASED;
     if (W->buf_f32 != (f32 ? 1 : 0)) {
         set_error(NAPSPMV_ERR_STATE, "the receive buffers hold the other precision's copies: "
                                      "apply once in this precision (phased or overlapped engine "
@@ -1903,10 +1968,10 @@ extern "C" int napspmv_spmv_step(napspmv_plan_t *P, napspmv_ws_t *ws, const doub
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((P->n + NT - 1) / NT,
                                                                   (int64_t)P->num_sms * 8));
         k_to_f32<<<g, NT, 0, (cudaStream_t)stream>>>(v, W->x32[0], P->n, W->err);
-        spmv_run(L, W->x32[0], W, w, nullptr, scale, o.stages, (cudaStream_t)stream);
+        spmv_run(L, W->x32[0], W, w, nullptr, scale, o.stages, (cudaStream_t)stream, pdl);
         count_launch(2);
     } else {
-        spmv_run(L, v, W, w, nullptr, scale, o.stages, (cudaStream_t)stream);
+        spmv_run(L, v, W, w, nullptr, scale, o.stages, (cudaStream_t)stream, pdl);
         count_launch(1);
     }
     NAP_CUDA(cudaGetLastError());
