@@ -206,7 +206,9 @@ __device__ __forceinline__ double f2d_exact(float f)
 
 // Batched element loop over [b, e): U independent index loads, then U
 // independent data loads, then U stores, per thread and step.
-template <int U, class T = double, class LoadIdx, class LoadVal, class Store>
+// WAIT: the index arrays are constant plan data, so the index loads are issued
+// before the programmatic-launch wait and only the value loads follow it.
+template <int U, class T = double, bool WAIT = false, class LoadIdx, class LoadVal, class Store>
 __device__ __forceinline__ void batched(int b, int e, int tid, LoadIdx li, LoadVal lv, Store st)
 {
     for (int base = b + tid; base < e; base += NT * U) {
@@ -217,6 +219,7 @@ __device__ __forceinline__ void batched(int b, int e, int tid, LoadIdx li, LoadV
             const int k = base + u * NT;
             if (k < e) ix[u] = li(k);
         }
+        if (WAIT) griddep_wait();
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const int k = base + u * NT;
@@ -691,34 +694,34 @@ __device__ __noinline__ void item_signal(const Job &J, const Item &it)
 
 // The element work of the message steps (shared by both engines; T = double,
 // or float for the FP32 copies of the phased engines' FP32 mode).
-template <bool INKERNEL, int U, class T = double>
+template <bool INKERNEL, int U, class T = double, bool WAIT = false>
 __device__ __noinline__ void step_gather(T *dst, const T *src, const int32_t *idx, int b, int e,
                                          int tid)
 {
     const uint64_t pol = policy_evict_first();
-    batched<U, T>(
+    batched<U, T, WAIT>(
         b, e, tid, [&](int k) { return (uint32_t)ld_stream_hint_s32(idx + k, pol); },
         [&](int, uint32_t j) { return ldx<INKERNEL>(src + j); },
         [&](int k, uint32_t, T v) { dst[k] = v; });
 }
-template <bool INKERNEL, int U, class T = double>
+template <bool INKERNEL, int U, class T = double, bool WAIT = false>
 __device__ __noinline__ void step_pack(T *gsend, const T *x, const T *lbuf, const uint32_t *src,
                                        int b, int e, int tid)
 {
     const uint64_t pol = policy_evict_first();
-    batched<U, T>(
+    batched<U, T, WAIT>(
         b, e, tid, [&](int k) { return ld_stream_hint_u32(src + k, pol); },
         [&](int, uint32_t u) {
             return (u & kFromLbuf) ? ldx<INKERNEL>(lbuf + (u & ~kFromLbuf)) : ldx<INKERNEL>(x + u);
         },
         [&](int k, uint32_t, T v) { gsend[k] = v; });
 }
-template <bool INKERNEL, int U, class T = double>
+template <bool INKERNEL, int U, class T = double, bool WAIT = false>
 __device__ __noinline__ void step_transfer(T *grecv, const T *gsend, const int32_t *dst, int b,
                                            int e, int tid)
 {
     const uint64_t pol = policy_evict_first();
-    batched<U, T>(
+    batched<U, T, WAIT>(
         b, e, tid, [&](int k) { return (uint32_t)ld_stream_hint_s32(dst + k, pol); },
         [&](int k, uint32_t) { return ldx<INKERNEL>(gsend + k); },
         [&](int, uint32_t d, T v) { grecv[d] = v; });
@@ -837,15 +840,17 @@ __global__ void __launch_bounds__(NT)
     k_gather2(const T *x, const int32_t *bll_j, T *bll, int n_bll, const int32_t *lbuf_j, T *lbuf,
               int n_lbuf, const int *err)
 {
-    griddep_wait();
-    if (*(volatile const int *)err) return;  // sticky error: no work until cleared
+    // sticky error: no work until cleared (a flag set by the programmatic
+    // predecessor itself is seen by the next launch)
+    if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n_bll + n_lbuf; b += gridDim.x * per) {
         const int e = min(b + per, n_bll + n_lbuf);
-        if (b < n_bll) step_gather<false, 8, T>(bll, x, bll_j, b, min(e, n_bll), threadIdx.x);
+        if (b < n_bll)
+            step_gather<false, 8, T, true>(bll, x, bll_j, b, min(e, n_bll), threadIdx.x);
         if (e > n_bll) {
             const int lb = max(b, n_bll) - n_bll, le = e - n_bll;
-            step_gather<false, 8, T>(lbuf, x, lbuf_j, lb, le, threadIdx.x);
+            step_gather<false, 8, T, true>(lbuf, x, lbuf_j, lb, le, threadIdx.x);
         }
     }
     griddep_done();
@@ -854,33 +859,30 @@ template <class T>
 __global__ void __launch_bounds__(NT)
     k_pack(const T *x, const T *lbuf, const uint32_t *src, T *gsend, int n, const int *err)
 {
-    griddep_wait();
     if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
-        step_pack<false, 8, T>(gsend, x, lbuf, src, b, min(b + per, n), threadIdx.x);
+        step_pack<false, 8, T, true>(gsend, x, lbuf, src, b, min(b + per, n), threadIdx.x);
     griddep_done();
 }
 template <class T>
 __global__ void __launch_bounds__(NT)
     k_transfer(const T *gsend, const int32_t *dst, T *grecv, int n, const int *err)
 {
-    griddep_wait();
     if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
-        step_transfer<false, 8, T>(grecv, gsend, dst, b, min(b + per, n), threadIdx.x);
+        step_transfer<false, 8, T, true>(grecv, gsend, dst, b, min(b + per, n), threadIdx.x);
     griddep_done();
 }
 template <class T>
 __global__ void __launch_bounds__(NT)
     k_unpack(const T *grecv, const int32_t *src, T *bnl, int n, const int *err)
 {
-    griddep_wait();
     if (*(volatile const int *)err) return;
     const int per = NT * 8;
     for (int b = blockIdx.x * per; b < n; b += gridDim.x * per)
-        step_gather<false, 8, T>(bnl, grecv, src, b, min(b + per, n), threadIdx.x);
+        step_gather<false, 8, T, true>(bnl, grecv, src, b, min(b + per, n), threadIdx.x);
     griddep_done();
 }
 // FP32 copy of an input vector (first apply of a chain in FP32 mode)
