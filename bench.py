@@ -260,10 +260,14 @@ def time_bounded(fn, budget_s):
     return reps, time.perf_counter() - t0
 
 
-def cpu_baseline_leg(A, v, w_gpu_one, B, budget_s):
+def cpu_baseline_leg(A, v, w_gpu_one, B, budget_s, n_p, ppn, strided=False):
     """The oracle timed on this host's cores on a bounded sample (single thread,
-    and on every core), and the relative error of one GPU apply against it."""
+    and on every core), its plan build timed once, and the relative error of one
+    GPU apply against it."""
     import oracle
+    t0 = time.perf_counter()
+    oracle.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=oracle.STRIDED if strided else 0)
+    plan_s = time.perf_counter() - t0
     ref = oracle.spmv(A.row_ptr, A.col, A.val, v)
     rel = float(np.linalg.norm(w_gpu_one - ref) / np.linalg.norm(ref))
     r1, e1 = time_bounded(lambda: oracle.spmv(A.row_ptr, A.col, A.val, v), budget_s / 2)
@@ -277,6 +281,7 @@ def cpu_baseline_leg(A, v, w_gpu_one, B, budget_s):
                       f"of equal stored entries, {eT:.1f} s), bytes counted as for the GPU apply",
             "single_thread": {"value": round(B * r1 / e1 / 1e9, 3), "cores": 1,
                               "sample": f"{r1} SpMVs in {e1:.1f} s"},
+            "plan_build_s": round(plan_s, 3),
             "gpu_vs_oracle_relerr": rel}
 
 
@@ -510,7 +515,8 @@ def main():
         "clocks": clocks,
     }
     if not args.no_cpu and ws == 1:
-        line["cpu_baseline"] = cpu_baseline_leg(A, v, w_one, B, args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline_leg(A, v, w_one, B, args.cpu_budget, w.n_p, w.ppn,
+                                                args.partition == "strided")
     if args.serve > 0 and ws == 1:
         from paper_1612_08060_gb300 import serve
         sweep = tuple(float(x) for x in args.serve_sweep.split(",") if x.strip())
