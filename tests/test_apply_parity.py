@@ -276,6 +276,24 @@ def test_workloads_full_size(cfg):
     assert_close_fp64(w, O.spmv(A.row_ptr, A.col, A.val, v), abs_row_bound(A, v))
 
 
+def test_config4_full_size():
+    """The 2^23-row banded random workload at full size (n_p 8192, ppn 32,
+    ~1.7e8 stored entries) with its default launch options (two lanes per row,
+    warp tiles, three CTAs per SM): one apply and a 3-apply chain, every output
+    element compared with the oracle."""
+    w_ = I.workload(4)
+    A = w_.build()
+    v = I.vector(A.n, w_.seed)
+    plan = gpu_plan(A, w_.n_p, w_.ppn)
+    d = nap.napspmv_get_default_opts(plan)
+    assert (d.vec, d.pipeline, d.ctas_per_sm) == (2, nap.PIPELINE_WARP, 3)
+    w = run(plan, v)
+    assert_close_fp64(w, O.spmv(A.row_ptr, A.col, A.val, v), abs_row_bound(A, v))
+    w = run(plan, v, reps=3, scale=1.0 / 64.0)
+    ref = oracle_chain(A, v, 3, 1.0 / 64.0)
+    assert np.linalg.norm(w - ref) <= 3e-13 * np.linalg.norm(ref)
+
+
 def test_config2_chain_bench_configuration():
     """The benchmark's step: 100 chained applies x <- A x / 16 of the 3D 7-point
     128^3 workload in one persistent launch; every element compared with the
