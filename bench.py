@@ -300,6 +300,9 @@ def main():
     ap.add_argument("--tile-nnz", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--pipeline", default="default", choices=["default", "cta", "warp"])
+    ap.add_argument("--halo", default="default", choices=["default", "on", "off"],
+                    help="overlapped engine: stage each process's receive buffers in shared "
+                         "memory for its remote rows")
     ap.add_argument("--gathers", default="literal", choices=["literal", "composed"],
                     help="composed: receive buffers gathered straight from v (an ablation "
                          "of the node-aware exchange's hops)")
@@ -378,6 +381,7 @@ def main():
                          tile_nnz=args.tile_nnz, stages=args.stages,
                          pipeline={"default": 0, "cta": nap.PIPELINE_CTA,
                                    "warp": nap.PIPELINE_WARP}[args.pipeline],
+                         halo={"default": 0, "on": nap.HALO_ON, "off": nap.HALO_OFF}[args.halo],
                          precision=nap.PREC_F32 if args.precision == "f32" else nap.PREC_F64,
                          ctas_per_sm=args.ctas_per_sm)
     eff = nap.napspmv_get_default_opts(plan)
@@ -490,6 +494,7 @@ def main():
                    "tile_nnz": opts.tile_nnz or eff.tile_nnz,
                    "stages": opts.stages or eff.stages,
                    "pipeline": {1: "cta", 2: "warp"}[opts.pipeline or eff.pipeline],
+                   "halo": {1: "on", 2: "off"}[opts.halo or eff.halo],
                    "l2": "inputs larger than L2: each apply streams the 175 MB col/val "
                          "arrays (L2 129 MB); not flushed between steps",
                    "parallelism": f"replicas{ws}"},

@@ -108,6 +108,11 @@ extern "C" {
 #define NAPSPMV_PIPELINE_CTA 1
 #define NAPSPMV_PIPELINE_WARP 2
 
+#define NAPSPMV_HALO_ON 1  /* overlapped engine: stage each process's receive
+                              buffers in shared memory for its remote rows when
+                              they fit (the default)                        */
+#define NAPSPMV_HALO_OFF 2 /* gather the receive buffers from global memory   */
+
 typedef struct napspmv_plan_s napspmv_plan_t;
 typedef struct napspmv_ws_s napspmv_ws_t;
 
@@ -146,6 +151,7 @@ typedef struct {
                             NAPSPMV_PIPELINE_WARP (each warp its own stages and
                             tiles of tile_rows / 8 rows, tile_nnz / 8 entries);
                             a CTA takes a contiguous run of tiles either way */
+    int32_t halo;        /* NAPSPMV_HALO_ON / _OFF (overlapped engine)         */
     int32_t timeout_ms;  /* limit of every device-side wait                    */
     int32_t debug_stall; /* test hook (fused engine): 1 makes the first work
                             item wait on a counter nothing increments, so the

@@ -951,6 +951,165 @@ __global__ void __launch_bounds__(NT)
     griddep_done();
 }
 
+// ------------------------------------------- remote pass with staged halos
+// The overlapped engine's remote part with each process's receive buffers
+// (its b_{l->l} and b_{nl->l} segments, contiguous in the workspace) staged in
+// shared memory.  A CTA's run of tiles is cut at process boundaries
+// (Item::msg = process); when the run enters a new process, one thread copies
+// that process's two segments, widened to 16-byte boundaries, into the window
+// with two bulk copies on their own mbarrier, and every remote gather of the
+// process's rows then reads shared memory: each received value is read from
+// global memory once per process, in order, instead of once per use.
+__host__ __device__ __forceinline__ int halo_align(int elem_bytes) { return 16 / elem_bytes; }
+
+template <int V, bool F32>
+__device__ __forceinline__ void tile_compute_halo(const TileStage &st, const void *win, int bll_lo,
+                                                  int nbw, int bnl_lo, double *y, float *y32,
+                                                  const Scale sc, int r0, int r1, int k0, int tid)
+{
+    using XT = typename std::conditional<F32, float, double>::type;
+    const XT *w = static_cast<const XT *>(win);
+    const int rb = r0 & ~3, kb = k0 & ~3;
+    const int nr = r1 - r0;
+    const int lane = tid & (V - 1), grp = tid / V, groups = NT / V;
+    const float *val32 = reinterpret_cast<const float *>(st.val);
+    for (int base = 0; base < nr; base += groups) {
+        const int i = base + grp;
+        double acc = 0.0;
+        if (i < nr && lane == 0) acc = ld_partial_f64(y + r0 + i);
+        if (i < nr) {
+            const int s = st.rows[r0 - rb + i] - kb, e = st.rows[r0 - rb + i + 1] - kb;
+#pragma unroll 8
+            for (int k = s + lane; k < e; k += V) {
+                const uint32_t c = st.col[k];
+                const int idx = (int)(c & kIndexMask);
+                const XT xv = (c >> kBlockShift) == 1 ? w[idx - bll_lo] : w[nbw + idx - bnl_lo];
+                acc = entry_add<F32>(acc, st.val, val32, k, xv);
+            }
+        }
+        if (V > 1) {
+#pragma unroll
+            for (int o = V / 2; o > 0; o >>= 1)
+                acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        }
+        if (i < nr && lane == 0) {
+            const double r = apply_scale(acc, sc);
+            y[r0 + i] = r;
+            if (y32) y32[r0 + i] = __double2float_rn(r);
+        }
+    }
+}
+
+template <int V, bool F32>
+__global__ void __launch_bounds__(NT)
+    k_spmv_halo(Csr3 A, const void *blls, const void *bnls, double *y, float *y32, Scale sc,
+                const Item *tiles, int n_tiles, int cap, int trows, int ns,
+                const int32_t *bll_rank, const int32_t *bnl_rank, int *err)
+{
+    using XT = typename std::conditional<F32, float, double>::type;
+    constexpr int VB = F32 ? 4 : 8;
+    const int AL = halo_align((int)sizeof(XT));
+    const XT *bll = static_cast<const XT *>(blls), *bnl = static_cast<const XT *>(bnls);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
+    griddep_wait();
+    if (*(volatile const int *)err) return;  // sticky error: no work until cleared
+    const int base_bytes = tile_smem_bytes(cap, trows, ns, VB);
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(smem + base_bytes);
+    XT *win = reinterpret_cast<XT *>(smem + base_bytes + 16);
+    if (tid == 0) mbar_init(wbar, 1);
+    tile_smem_init(smem, ns);  // the stage barriers, fence and CTA barrier
+    double *red = tile_red(smem, cap, trows, ns, VB);
+    TileStage wst{};
+    wst.bar = wbar;
+    uint32_t phase = 0, wphase = 0;
+    int cur_rank = -1, bll_lo = 0, nbw = 0, bnl_lo = 0;
+    bool wok = false;
+    const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+    const int q0 = blockIdx.x * per, q1 = min(n_tiles, q0 + per);
+    if (tid == 0)
+        for (int i = 0; i < ns - 1; i++) {
+            const int q = q0 + i;
+            if (q >= q1) break;
+            const Item it = tiles[q];
+            if (staged_tile(it, cap))
+                tile_issue<F32>(A, tile_stage(smem, i, cap, trows, VB), it.b, it.e, it.k0, it.k1);
+        }
+    int cur = 0;
+    for (int q = q0; q < q1; q++) {
+        const Item it = tiles[q];
+        const int qa = q + (ns - 1);
+        if (tid == 0 && qa < q1) {
+            const Item ita = tiles[qa];
+            const int sa = (cur + ns - 1) % ns;
+            if (staged_tile(ita, cap))
+                tile_issue<F32>(A, tile_stage(smem, sa, cap, trows, VB), ita.b, ita.e, ita.k0,
+                                ita.k1);
+        }
+        if (it.msg != cur_rank) {
+            // every thread finished the previous tile (CTA barrier at the end of
+            // the last iteration): the window may be refilled
+            const int t = it.msg;
+            const int b0 = bll_rank[t] & ~(AL - 1), b1 = (bll_rank[t + 1] + AL - 1) & ~(AL - 1);
+            const int n0 = bnl_rank[t] & ~(AL - 1), n1 = (bnl_rank[t + 1] + AL - 1) & ~(AL - 1);
+            if (tid == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(wbar, (uint32_t)((b1 - b0) + (n1 - n0)) * (uint32_t)sizeof(XT));
+                if (b1 > b0) bulk_g2s(win, bll + b0, (uint32_t)(b1 - b0) * sizeof(XT), wbar);
+                if (n1 > n0)
+                    bulk_g2s(win + (b1 - b0), bnl + n0, (uint32_t)(n1 - n0) * sizeof(XT), wbar);
+            }
+            bll_lo = b0;
+            nbw = b1 - b0;
+            bnl_lo = n0;
+            wok = tile_wait(wst, wphase, err);
+            wphase ^= 1;
+            cur_rank = t;
+        }
+        if (staged_tile(it, cap)) {
+            const TileStage st = tile_stage(smem, cur, cap, trows, VB);
+            const bool ok = tile_wait(st, (phase >> cur) & 1, err);
+            phase ^= 1u << cur;
+            if (ok && wok)
+                tile_compute_halo<V, F32>(st, win, bll_lo, nbw, bnl_lo, y, y32, sc, it.b, it.e,
+                                          it.k0, tid);
+        } else if (wok) {
+            // a row longer than a stage: entries from global memory, values
+            // from the window (the whole CTA on the row, fixed-order tree)
+            for (int r = it.b; r < it.e; r++) {
+                const int s0 = ld_stream_s32(A.rowptr + r), e0 = ld_stream_s32(A.rowptr + r + 1);
+                double acc = 0.0;
+                for (int k = s0 + tid; k < e0; k += NT) {
+                    const uint32_t c = ld_stream_u32(A.colenc + k);
+                    const int idx = (int)(c & kIndexMask);
+                    const XT xv = (c >> kBlockShift) == 1 ? win[idx - bll_lo]
+                                                          : win[nbw + idx - bnl_lo];
+                    if constexpr (F32)
+                        acc = __dadd_rn(acc, f32_product(ld_stream_f32(A.val32 + k), xv));
+                    else
+                        acc = fma(ld_stream_f64(A.val + k), xv, acc);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+                if ((tid & 31) == 0) red[tid >> 5] = acc;
+                __syncthreads();
+                if (tid == 0) {
+                    double t2 = ld_partial_f64(y + r);
+                    for (int w2 = 0; w2 < NT / 32; w2++) t2 = __dadd_rn(t2, red[w2]);
+                    const double res = apply_scale(t2, sc);
+                    y[r] = res;
+                    if (y32) y32[r] = __double2float_rn(res);
+                }
+                __syncthreads();
+            }
+        }
+        cur = cur + 1 == ns ? 0 : cur + 1;
+        __syncthreads();
+    }
+    griddep_done();
+}
+
 // ----------------------------------------------- warp-pipelined SpMV
 // Each warp owns `ns` shared-memory stages with their own mbarriers and
 // streams its own tiles (at most 32 / V rows and `capw` entries): lane 0
@@ -1117,6 +1276,7 @@ napspmv_opts resolve_opts(const napspmv_plan_t *P, const napspmv_opts *o)
     if (o->tile_nnz) r.tile_nnz = o->tile_nnz;
     if (o->stages) r.stages = o->stages;
     if (o->pipeline) r.pipeline = o->pipeline;
+    if (o->halo) r.halo = o->halo;
     if (o->timeout_ms) r.timeout_ms = o->timeout_ms;
     r.debug_stall = o->debug_stall;
     return r;
@@ -1205,10 +1365,28 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
             r = e;
         }
     };
-    std::vector<Item> tl, tr;
+    std::vector<Item> tl, tr, trh;
     if (!P->h_rowptrL.empty()) {
         cut(P->h_rowptrL, tl);
         cut(P->h_rowptrR, tr);
+        if (!(P->flags & NAPSPMV_PARTITION_STRIDED)) {
+            // remote tiles never straddle two processes: Item::msg is the
+            // process, whose receive buffers the remote pass may stage
+            const int64_t n = P->n, q = n / P->np, rem = n % P->np;
+            std::vector<int32_t> sub;
+            for (int32_t r = 0; r < P->np; r++) {
+                const int64_t r0 = r * q + std::min<int64_t>(r, rem);
+                const int64_t r1 = r0 + q + (r < rem ? 1 : 0);
+                sub.assign(P->h_rowptrR.begin() + r0, P->h_rowptrR.begin() + r1 + 1);
+                const size_t first = trh.size();
+                cut(sub, trh);
+                for (size_t k = first; k < trh.size(); k++) {
+                    trh[k].b += (int32_t)r0;
+                    trh[k].e += (int32_t)r0;
+                    trh[k].msg = r;
+                }
+            }
+        }
     }
     // warp tiles: the same cutting with a warp's share of a CTA tile
     std::vector<Item> wt, wtl, wtr;
@@ -1241,6 +1419,7 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
         fit(whole, tile_nnz, S.fit_nnz[0], S.fit_rows[0]);
         fit(tl, tile_nnz, S.fit_nnz[1], S.fit_rows[1]);
         fit(tr, tile_nnz, S.fit_nnz[2], S.fit_rows[2]);
+        fit(trh, tile_nnz, S.fit_nnz[6], S.fit_rows[6]);
         fit(wt, wn, S.fit_nnz[3], S.fit_rows[3]);
         fit(wtl, wn, S.fit_nnz[4], S.fit_rows[4]);
         fit(wtr, wn, S.fit_nnz[5], S.fit_rows[5]);
@@ -1255,6 +1434,7 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
         return NAPSPMV_OK;
     };
     if (int rc = upload_items(wt, &S.d_wt, &S.n_wt)) return rc;
+    if (int rc = upload_items(trh, &S.d_tilesRH, &S.n_tilesRH)) return rc;
     if (int rc = upload_items(wtl, &S.d_wtL, &S.n_wtL)) return rc;
     if (int rc = upload_items(wtr, &S.d_wtR, &S.n_wtR)) return rc;
     Item *d_tl = nullptr, *d_tr = nullptr;
@@ -1303,8 +1483,10 @@ int ws_alloc(napspmv_plan_t *P, napspmv_ws_t *ws)
     auto alf = [](float **p, int64_t n) {
         return cudaMalloc(p, sizeof(float) * (size_t)std::max<int64_t>(n, 1));
     };
-    if (al(&ws->bll, P->n_bll) || al(&ws->lbuf, P->n_lbuf) || al(&ws->gsend, P->n_gs) ||
-        al(&ws->grecv, P->n_gs) || al(&ws->bnl, P->n_bnl) || al(&ws->xtmp, P->n) ||
+    // b_{l->l} and b_{nl->l} get 4 spare values: the remote pass copies each
+    // process's segment widened to 16-byte boundaries
+    if (al(&ws->bll, P->n_bll + 4) || al(&ws->lbuf, P->n_lbuf) || al(&ws->gsend, P->n_gs) ||
+        al(&ws->grecv, P->n_gs) || al(&ws->bnl, P->n_bnl + 4) || al(&ws->xtmp, P->n) ||
         alf(&ws->x32[0], P->n) || alf(&ws->x32[1], P->n) ||
         cudaMalloc(&ws->ctr, sizeof(unsigned long long) * ctr_count(P)) ||
         cudaMalloc(&ws->err, sizeof(int))) {
@@ -1440,13 +1622,63 @@ static SpmvKernel pick_spmv(int vec, bool warp = false)
 
 // Kernel, tiles, capacities, shared memory and grid of one SpMV launch
 // (mode: full three-block pass, local part, remote part).
+using HaloKernel = void (*)(Csr3, const void *, const void *, double *, float *, Scale,
+                           const Item *, int, int, int, int, const int32_t *, const int32_t *,
+                           int *);
+template <bool F32>
+static HaloKernel pick_halo(int vec)
+{
+    switch (vec) {
+    case 1: return k_spmv_halo<1, F32>;
+    case 2: return k_spmv_halo<2, F32>;
+    case 4: return k_spmv_halo<4, F32>;
+    case 8: return k_spmv_halo<8, F32>;
+    case 16: return k_spmv_halo<16, F32>;
+    default: return k_spmv_halo<32, F32>;
+    }
+}
+
 struct SpmvLaunch {
     SpmvKernel fn = nullptr;
+    HaloKernel hfn = nullptr;  // set: the remote pass with staged receive buffers
     Csr3 A{};
     const Item *tiles = nullptr;
+    const int32_t *bll_rank = nullptr, *bnl_rank = nullptr;
     int n = 0, cap = 0, rows = 0, grid = 1;
     size_t sm = 0;
 };
+
+// Shared memory of the staged-halo remote pass, or 0 if it does not apply:
+// CTA stages for the remote tiles plus the widest process window.  It applies
+// where the remote rows are gather-heavy (at least 8 remote entries per row on
+// average) and two CTAs still fit on an SM.  Measured: the 2^23-row banded
+// random workload (about 19 remote entries per row) gains 14% per apply in
+// FP32 mode (70 KB windows, two CTAs per SM), breaks even in FP64 (136 KB, one
+// CTA per SM); the stencils (2-6 remote entries per row) lose 5-7%.
+static size_t halo_smem(const napspmv_plan_t *P, const napspmv_opts &o)
+{
+    if (o.halo != NAPSPMV_HALO_ON || (P->flags & NAPSPMV_PARTITION_STRIDED) ||
+        P->h_bll_rank.size() != (size_t)P->np + 1 || P->items.n_tilesRH == 0 ||
+        P->nnzR < 8 * P->n)
+        return 0;
+    const bool f32 = o.precision == NAPSPMV_PREC_F32;
+    const int es = f32 ? 4 : 8, al = halo_align(es);
+    int64_t wcap = 0;
+    for (int32_t r = 0; r < P->np; r++) {
+        const int64_t b0 = P->h_bll_rank[r] & ~(al - 1);
+        const int64_t b1 = (P->h_bll_rank[r + 1] + al - 1) & ~(al - 1);
+        const int64_t n0 = P->h_bnl_rank[r] & ~(al - 1);
+        const int64_t n1 = (P->h_bnl_rank[r + 1] + al - 1) & ~(al - 1);
+        wcap = std::max(wcap, (b1 - b0) + (n1 - n0));
+    }
+    const size_t sm = (size_t)tile_smem_bytes(P->items.fit_nnz[6], P->items.fit_rows[6], o.stages,
+                                              es) + 16 + (size_t)wcap * es;
+    int smem_sm = 0, reserved = 0;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, P->device) ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, P->device))
+        return 0;
+    return 2 * (sm + (size_t)reserved) <= (size_t)smem_sm ? sm : 0;
+}
 static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode, SpmvLaunch &L)
 {
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
@@ -1465,20 +1697,35 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
         L.n = warp ? S.n_wtL : S.n_tilesL;
     } else if (mode == kRemote) {
         L.A = Csr3{P->d_rowptrR, P->d_colR, P->d_valR, f32 ? P->d_val32R : nullptr};
-        L.fn = f32 ? pick_spmv<true, kRemote>(o.vec, warp) : pick_spmv<false, kRemote>(o.vec, warp);
-        L.tiles = warp ? S.d_wtR : S.d_tilesR;
-        L.n = warp ? S.n_wtR : S.n_tilesR;
+        if (const size_t hs = halo_smem(P, o)) {
+            // CTA tiles cut at process boundaries, receive buffers staged
+            L.hfn = f32 ? pick_halo<true>(o.vec) : pick_halo<false>(o.vec);
+            L.cap = S.fit_nnz[6];
+            L.rows = S.fit_rows[6];
+            L.sm = hs;
+            L.tiles = S.d_tilesRH;
+            L.n = S.n_tilesRH;
+            L.bll_rank = P->d_bll_rank;
+            L.bnl_rank = P->d_bnl_rank;
+        } else {
+            L.fn = f32 ? pick_spmv<true, kRemote>(o.vec, warp)
+                       : pick_spmv<false, kRemote>(o.vec, warp);
+            L.tiles = warp ? S.d_wtR : S.d_tilesR;
+            L.n = warp ? S.n_wtR : S.n_tilesR;
+        }
     } else {
         L.A = Csr3{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
         L.fn = f32 ? pick_spmv<true, kFull>(o.vec, warp) : pick_spmv<false, kFull>(o.vec, warp);
         L.tiles = warp ? S.d_wt : S.d_items + S.spmv_first;
         L.n = warp ? S.n_wt : S.n_items - S.spmv_first;
     }
-    if (int rc = prepare_smem(L.fn, L.sm)) return rc;
+    const void *kf = L.hfn ? (const void *)L.hfn : (const void *)L.fn;
+    if (L.sm > 48 * 1024)
+        NAP_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.sm));
     int occ = 0;
-    NAP_CUDA(cudaFuncSetAttribute(L.fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+    NAP_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));
-    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, NT, L.sm));
+    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf, NT, L.sm));
     // resident CTAs per SM: the occupancy maximum, or fewer (ctas_per_sm) where
     // the gathers want L1 more than the extra warps
     if (o.ctas_per_sm > 0) occ = std::min(occ, o.ctas_per_sm);
@@ -1492,9 +1739,9 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
                                         P->device));
         const int64_t need = (int64_t)std::max(occ, 1) * ((int64_t)L.sm + reserved);
         const int pct = (int)std::min<int64_t>(100, (need * 100 + smem_sm - 1) / smem_sm);
-        NAP_CUDA(cudaFuncSetAttribute(L.fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+        NAP_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
     }
-    const int ctas = warp ? (L.n + WPB - 1) / WPB : L.n;
+    const int ctas = (warp && !L.hfn) ? (L.n + WPB - 1) / WPB : L.n;
     L.grid = std::max(1, std::min(ctas, P->num_sms * std::max(occ, 1)));
     if (mode == kLocal)  // leave one CTA slot per SM for the message steps
         L.grid = std::max(1, std::min(ctas, P->num_sms * std::max(occ - 1, 1)));
@@ -1527,8 +1774,14 @@ static void launch_pdl(bool pdl, void (*kern)(KArgs...), int grid, size_t smem, 
 static void spmv_run(const SpmvLaunch &L, const void *x, const napspmv_ws_t *ws, double *y,
                      float *y32, double scale, int stages, cudaStream_t s, bool pdl)
 {
-    launch_pdl(pdl, L.fn, L.grid, L.sm, s, L.A, x, (const void *)ws->bll, (const void *)ws->bnl, y, y32,
-               make_scale(scale), L.tiles, L.n, L.cap, L.rows, stages, ws->err);
+    if (L.hfn)
+        launch_pdl(pdl, L.hfn, L.grid, L.sm, s, L.A, (const void *)ws->bll, (const void *)ws->bnl,
+                   y, y32, make_scale(scale), L.tiles, L.n, L.cap, L.rows, stages, L.bll_rank,
+                   L.bnl_rank, ws->err);
+    else
+        launch_pdl(pdl, L.fn, L.grid, L.sm, s, L.A, x, (const void *)ws->bll,
+                   (const void *)ws->bnl, y, y32, make_scale(scale), L.tiles, L.n, L.cap, L.rows,
+                   stages, ws->err);
 }
 
 // The four message steps of one apply (phases 1-4) as kernels on stream s;
@@ -1686,7 +1939,7 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
         if (g.v == v && g.w == w && g.ws == ws && g.reps == reps && g.scale == scale &&
             g.prec == o.precision && g.vec == o.vec && g.tile_rows == o.tile_rows &&
             g.tile_nnz == o.tile_nnz && g.engine == o.engine && g.stages == o.stages &&
-            g.pipeline == o.pipeline && g.ctas_per_sm == o.ctas_per_sm) {
+            g.pipeline == o.pipeline && g.ctas_per_sm == o.ctas_per_sm && g.halo == o.halo) {
             NAP_CUDA(cudaGraphLaunch(g.exec, s));
             count_launch(g.kernels);
             return NAPSPMV_OK;
@@ -1710,7 +1963,7 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
         P->graphs.erase(P->graphs.begin());
     }
     P->graphs.push_back({v, w, ws, reps, o.precision, o.vec, o.tile_rows, o.tile_nnz, o.engine,
-                         o.stages, o.pipeline, o.ctas_per_sm, scale, exec, nk});
+                         o.stages, o.pipeline, o.ctas_per_sm, o.halo, scale, exec, nk});
     NAP_CUDA(cudaGraphLaunch(exec, s));
     count_launch(nk);
     return NAPSPMV_OK;
@@ -1747,6 +2000,10 @@ static int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
     }
     if (o.timeout_ms < 1) {
         set_error(NAPSPMV_ERR_ARG, "timeout_ms must be >= 1");
+        return NAPSPMV_ERR_ARG;
+    }
+    if (o.halo != NAPSPMV_HALO_ON && o.halo != NAPSPMV_HALO_OFF) {
+        set_error(NAPSPMV_ERR_ARG, "halo must be NAPSPMV_HALO_ON or _OFF");
         return NAPSPMV_ERR_ARG;
     }
     if (o.pipeline != NAPSPMV_PIPELINE_CTA && o.pipeline != NAPSPMV_PIPELINE_WARP) {

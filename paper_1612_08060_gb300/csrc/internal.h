@@ -64,14 +64,18 @@ struct ItemSet {
     int32_t spmv_first = 0;  // items [spmv_first, n_items) are the row tiles
     Item *d_tilesL = nullptr, *d_tilesR = nullptr;  // tiles of the split parts
     int32_t n_tilesL = 0, n_tilesR = 0;
+    // remote tiles cut at process boundaries (Item::msg = process), for the
+    // remote pass with staged receive buffers
+    Item *d_tilesRH = nullptr;
+    int32_t n_tilesRH = 0;
     // warp tiles (at most tile_rows / 8 rows, tile_nnz / 8 entries) of the whole
     // matrix and of its two split parts
     Item *d_wt = nullptr, *d_wtL = nullptr, *d_wtR = nullptr;
     int32_t n_wt = 0, n_wtL = 0, n_wtR = 0;
     // largest staged tile (entries, rows) of each list, in the order whole /
-    // local / remote CTA tiles, then whole / local / remote warp tiles: a
-    // stage is sized to what its list needs, not to tile_nnz
-    int32_t fit_nnz[6] = {}, fit_rows[6] = {};
+    // local / remote CTA tiles, whole / local / remote warp tiles, remote tiles
+    // cut per process: a stage is sized to what its list needs, not to tile_nnz
+    int32_t fit_nnz[7] = {}, fit_rows[7] = {};
     Item *d_items = nullptr;
     // per-apply increments of every counter, [kNumCounters][nn]
     uint64_t *d_cnt = nullptr;
@@ -131,6 +135,9 @@ struct napspmv_plan_s {
     double *d_valL = nullptr, *d_valR = nullptr;
     float *d_val32L = nullptr, *d_val32R = nullptr;
     std::vector<int32_t> h_rowptrL, h_rowptrR;
+    // per-process offsets of b_{l->l} and b_{nl->l} (np + 1 each), host and device
+    std::vector<int32_t> h_bll_rank, h_bnl_rank;
+    int32_t *d_bll_rank = nullptr, *d_bnl_rank = nullptr;
     cudaStream_t aux = nullptr;  // low-priority stream of the local SpMV
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
@@ -153,7 +160,7 @@ struct napspmv_plan_s {
     // instantiated CUDA graphs of chained phased applies, newest last
     struct GraphEntry {
         const void *v, *w, *ws;
-        int32_t reps, prec, vec, tile_rows, tile_nnz, engine, stages, pipeline, ctas_per_sm;
+        int32_t reps, prec, vec, tile_rows, tile_nnz, engine, stages, pipeline, ctas_per_sm, halo;
         double scale;
         cudaGraphExec_t exec;
         int64_t kernels;

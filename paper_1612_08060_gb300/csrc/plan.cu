@@ -889,6 +889,10 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
     std::vector<int32_t> lbuf_ptr = full_ptr(P->lists[L_LBUF], np);
     std::vector<int32_t> bll_ptr = full_ptr(P->lists[L_BLL], np);
     std::vector<int32_t> bnl_ptr = full_ptr(P->lists[L_BNL], np);
+    P->h_bll_rank = bll_ptr;
+    P->h_bnl_rank = bnl_ptr;
+    P->d_bll_rank = upload(bll_ptr);
+    P->d_bnl_rank = upload(bnl_ptr);
     dvec<int32_t> d_lbuf_ptr, d_bll_ptr, d_bnl_ptr;
     d_lbuf_ptr.p = upload(lbuf_ptr);
     d_bll_ptr.p = upload(bll_ptr);
@@ -1049,9 +1053,9 @@ void plan_free(napspmv_plan_t *P)
     void *ptrs[] = {P->d_split, P->d_rowptr, P->d_colenc, P->d_val, P->d_val32, P->d_pack_src,
                     P->d_xfer_dst, P->d_unp_src, P->d_gs_msg_off, P->d_gs_msg_dstnode,
                     P->items.d_items, P->items.d_cnt, P->items.d_tilesL, P->items.d_tilesR,
-                    P->items.d_wt, P->items.d_wtL, P->items.d_wtR,
+                    P->items.d_wt, P->items.d_wtL, P->items.d_wtR, P->items.d_tilesRH,
                     P->d_rowptrL, P->d_rowptrR, P->d_colL, P->d_colR, P->d_valL, P->d_valR,
-                    P->d_val32L, P->d_val32R};
+                    P->d_val32L, P->d_val32R, P->d_bll_rank, P->d_bnl_rank};
     if (P->aux) cudaStreamDestroy(P->aux);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
@@ -1137,6 +1141,7 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         P->defaults.tile_nnz = cap;
         P->defaults.stages = 2;
         P->defaults.pipeline = pipeline;
+        P->defaults.halo = NAPSPMV_HALO_ON;
         P->defaults.timeout_ms = 10000;
         P->defaults.debug_stall = 0;
         rc = build_items(P, P->defaults.chunk, P->defaults.tile_rows, P->defaults.tile_nnz);

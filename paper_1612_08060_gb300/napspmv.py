@@ -21,6 +21,7 @@ F32_VALUES, MAP_TEXT, PARTITION_STRIDED, MAP_MAJORITY, COMPOSED_GATHERS = 1, 2, 
 PREC_F64, PREC_F32 = 0, 1
 ENGINE_DEFAULT, ENGINE_FUSED, ENGINE_PHASED, ENGINE_OVERLAP = 0, 1, 2, 3
 PIPELINE_CTA, PIPELINE_WARP = 1, 2
+HALO_ON, HALO_OFF = 1, 2
 (LIST_STD, LIST_NODE, LIST_INTER, LIST_J0, LIST_J1, LIST_J2, LIST_BLL, LIST_BNL, LIST_LBUF,
  LIST_TU, LIST_SPLIT) = range(11)
 
@@ -40,7 +41,7 @@ class napspmv_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("engine", C.c_int32), ("vec", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("chunk", C.c_int32), ("tile_rows", C.c_int32),
                 ("tile_nnz", C.c_int32), ("stages", C.c_int32), ("pipeline", C.c_int32),
-                ("timeout_ms", C.c_int32), ("debug_stall", C.c_int32)]
+                ("halo", C.c_int32), ("timeout_ms", C.c_int32), ("debug_stall", C.c_int32)]
 
 
 STAT_FIELDS = [

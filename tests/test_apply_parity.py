@@ -230,6 +230,32 @@ def test_composed_gathers_engine_limits():
         assert e.value.code == nap.ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("prec", [nap.PREC_F64, nap.PREC_F32])
+@pytest.mark.parametrize("vec", [1, 2, 8])
+@pytest.mark.parametrize("case", ["random", "poisson3d", "banded"])
+def test_halo_staging_same_bits(case, vec, prec):
+    """The overlapped engine's remote pass with each process's receive buffers
+    staged in shared memory (the default) against gathers from global memory:
+    same values in the same order, identical bits; both within the oracle's
+    tolerance."""
+    if case == "random":
+        A, n_p, ppn = I.random_pattern(700, 0.02, 51), 33, 4
+    elif case == "poisson3d":
+        A, n_p, ppn = I.poisson3d(24), 54, 6
+    else:
+        w_ = I.workload(4, 64)
+        A, n_p, ppn = w_.build(), w_.n_p, w_.ppn
+    v = I.vector(A.n, 52)
+    plan = gpu_plan(A, n_p, ppn)
+    o = dict(engine=nap.ENGINE_OVERLAP, vec=vec, precision=prec, reps=2, scale=0.5)
+    a = run(plan, v, halo=nap.HALO_ON, **o)
+    b = run(plan, v, halo=nap.HALO_OFF, **o)
+    assert np.array_equal(a, b)
+    if prec == nap.PREC_F64:
+        ref = oracle_chain(A, v, 2, 0.5)
+        assert np.linalg.norm(a - ref) <= 2e-13 * np.linalg.norm(ref)
+
+
 def test_strided_partition_engine_limits():
     """The fused engine cuts SpMV items per node, which a strided partition has
     no contiguous rows for: fused applies, batches and the no-allocation entry
