@@ -481,6 +481,7 @@ def main():
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+        "ms_per_step_median": round(statistics.median(per), 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32-values/f64-sums" if f32 else "f64", "data": "synthetic",
         "config": {"workload": w.name + ("_strided" if args.partition == "strided" else "") + (
