@@ -1125,7 +1125,7 @@ __host__ __device__ __forceinline__ int warp_smem_bytes(int capw, int rowsw, int
 }
 
 template <int V, bool F32, int MODE>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
     k_spmv_w(Csr3 A, const void *xs, const void *blls, const void *bnls, double *y, float *y32,
              Scale sc, const Item *tiles, int n_tiles, int capw, int rowsw, int ns, int *err)
 {
