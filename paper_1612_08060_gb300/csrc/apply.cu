@@ -1748,7 +1748,7 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
     return NAPSPMV_OK;
 }
 // Launch with programmatic stream serialization: the kernel may become
-// resident while its stream predecessor drains (it waits in griddep_enter).
+// resident while its stream predecessor drains (it waits in griddep_wait).
 // Errors surface through cudaGetLastError like a <<<>>> launch.
 // pdl = false: an ordinary launch.
 template <typename... KArgs, typename... Args>
