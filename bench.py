@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "NAPSpMV GB/s (% of HBM peak); served p50/p99 vs plain loop at stated rel err"
+NOMINAL_GBS = 8000.0  # GB300 HBM3e nominal bandwidth, beside the measured copy peak
 SCALE = 1.0 / 16.0  # power of two (exact scaling); the 7-point max row sum of |A| is 12
 
 
@@ -511,11 +512,13 @@ def main():
         "roofline": {"bound": "hbm", "achieved": round(B_spmv / (spmv_ms * 1e-3) / 1e9, 3),
                      "peak": peak, "unit": "GB/s",
                      "frac": round(B_spmv / (spmv_ms * 1e-3) / 1e9 / peak, 4),
+                     "frac_of_nominal_8tbs": round(B_spmv / (spmv_ms * 1e-3) / 1e9 / NOMINAL_GBS, 4),
                      "peak_kind": peak_kind, "traffic": ncu_traffic(),
                      "kernel": "k_spmv (three-block SpMV step, one launch = one apply's rows)",
                      "algorithmic_bytes": B_spmv, "launch_ms": round(spmv_ms, 5)},
         "step_roofline": {"bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
                           "frac": round(achieved / peak, 4),
+                          "frac_of_nominal_8tbs": round(achieved / NOMINAL_GBS, 4),
                           "what": "whole apply (message steps + SpMV), algorithmic bytes"},
         "gpu_launches": int(launches),
         "plan": {"gpu_plan_ms": round(plan_ms, 2), "std_msgs": st["std_msgs"],
