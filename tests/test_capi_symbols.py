@@ -54,6 +54,31 @@ def test_strerror_and_argument_errors_without_gpu(libpath):
     assert b"invalid CSR" in nap.lib().napspmv_last_error()
 
 
+def test_limits_and_flags_rejected_before_device_work(libpath):
+    """Size limits, partition bounds and plan flags are checked on the host
+    before the arrays are read: a descriptor claiming N = 2^30 over a tiny
+    buffer is refused with ERR_UNSUPPORTED, never dereferenced."""
+    import numpy as np
+    from paper_1612_08060_gb300 import napspmv as nap
+    rp = np.zeros(4, np.int64)
+    col = np.zeros(1, np.int32)
+    val = np.zeros(1, np.float64)
+
+    def plan(n, nnz, n_p, ppn, flags=0):
+        csr = nap.napspmv_csr(n, nnz, rp.ctypes.data, col.ctypes.data, val.ctypes.data, nap.HOST)
+        h = ctypes.c_void_p()
+        return nap.lib().napspmv_plan(ctypes.byref(csr), n_p, ppn, flags, ctypes.byref(h))
+
+    assert plan(1 << 30, 0, 4, 2) == nap.ERR_UNSUPPORTED
+    assert plan(3, (1 << 31) - 1, 1, 1) == nap.ERR_UNSUPPORTED
+    assert plan(3, 0, 4, 2) == nap.ERR_ARG          # n_p > N
+    assert plan(3, 0, 0, 2) == nap.ERR_ARG          # n_p < 1
+    assert plan(3, 0, 2, 0) == nap.ERR_ARG          # ppn < 1
+    assert plan(3, 0, 2, 1, 32) == nap.ERR_ARG      # unknown flag bit
+    assert plan(3, 0, 2, 1, nap.MAP_TEXT | nap.MAP_MAJORITY) == nap.ERR_ARG
+    assert b"exclude each other" in nap.lib().napspmv_last_error()
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_1612_08060_gb300 import napspmv as nap
     monkeypatch.setattr(nap, "_lib", None)
