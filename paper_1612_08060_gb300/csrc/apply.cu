@@ -12,22 +12,34 @@
 //            off_node from b_{nl->l} (the three local_spmv of the algorithm as
 //            one pass over each row, blocks in that order)
 //
-// Fused engine: one persistent launch.  CTAs take work items (chunks of a
-// node's gather ranges, tiles of a node's rows) from a global ticket counter
-// in topological order; before an item runs, thread 0 waits (bounded, with a
-// device error flag on timeout) on per-node counters of the items it depends
-// on, so node n's SpMV starts as soon as node n's buffers are complete and a
-// chain of applies x_{k+1} = scale A x_k pipelines across nodes.  Tickets are
-// handed out in order and an item only waits on earlier tickets, so progress
-// never depends on how many CTAs are resident.
+// Row tiles (all engines): one thread copies a tile's row-pointer, column and
+// value slices into a shared-memory stage with bulk asynchronous copies counted
+// on an mbarrier; the next tile's copy overlaps the current tile.  Each row is
+// then summed from shared memory by one lane (vec lanes for long rows) with x
+// and the receive buffers gathered from L2/HBM: one DFMA per stored entry (FP64
+// issue, not only HBM, bounds the SpMV on GB300).  Stages are sized to each
+// tile list's largest tile; tiles are handed to CTAs in contiguous runs; a CTA
+// pipeline and a warp pipeline (each warp its own stages) are provided.
 //
-// A row tile is evaluated in two passes: every thread forms products
-// a_k * x_{c_k} of the tile's entries with independent loads (coalesced
-// column/value streams, gathered x) into shared memory, then the rows are
-// summed from shared memory in stored order.
-//
-// Phased engine (control): one kernel per phase per apply, same tiles and the
-// same arithmetic, so the two engines agree bit for bit.
+// Engines:
+//   overlapped (default)  the matrix split into its on_process part (local,
+//       needs no message) and its remote part; the local pass runs on a second
+//       stream while the message steps run, the remote pass continues each
+//       row's FMA chain from the local partial.  Where remote rows are
+//       gather-heavy, the remote pass stages each process's receive buffers in
+//       shared memory.
+//   phased   one kernel per phase per apply with the single-pass SpMV.
+//   fused    one persistent launch for all phases and applies: CTAs take work
+//       items (chunks of a node's gather ranges, tiles of a node's rows) from a
+//       global ticket counter in topological order; before an item runs,
+//       thread 0 waits (bounded, with a device error flag on timeout) on
+//       per-node counters of the items it depends on.  Tickets are handed out
+//       in order and an item only waits on earlier tickets, so progress never
+//       depends on how many CTAs are resident.  It also runs batches of
+//       independent applies in one launch.
+// The phased engines capture chained applies into CUDA graphs and launch
+// dependent kernels programmatically (resident while the predecessor drains).
+// With one lane per row every engine gives the same bits.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
