@@ -10,8 +10,12 @@
 //   (q, s, j)  off_node -> on_node                              Eqs. L1, IL1
 // built with CUB radix sort / select / run-length encode (library primitives
 // for plan time only; the apply path is hand-written).  The per-node-pair
-// process assignment T/U (Eqs. T, U and the mapping rule after them) is
-// O(node pairs) and runs on the host.
+// process assignment T/U (Eqs. T, U and the mapping rule after them, the
+// text's variant, or the majority mapping whose per-pair counts are taken on
+// the device) is O(node pairs) and runs on the host.  The owner of a row or
+// column follows the plan's partition: contiguous blocks (Eq. R) or strided
+// (row i on process i mod n_p).  The plan also keeps the matrix split into its
+// on_process and remote parts for the overlapped engine.
 #include <cub/cub.cuh>
 
 #include <algorithm>
