@@ -515,6 +515,10 @@ def main():
                      "frac_of_nominal_8tbs": round(B_spmv / (spmv_ms * 1e-3) / 1e9 / NOMINAL_GBS, 4),
                      "peak_kind": peak_kind, "traffic": ncu_traffic(),
                      "kernel": "k_spmv (three-block SpMV step, one launch = one apply's rows)",
+                     "timing": "CUDA events around 50 back-to-back napspmv_spmv_step launches on "
+                               "the benchmark stream after the timed region; inside it the "
+                               "overlapped engine runs the same rows as a local and a remote "
+                               "launch (shares in profiles/overlap_engine_128cube_launches.md)",
                      "algorithmic_bytes": B_spmv, "launch_ms": round(spmv_ms, 5)},
         "step_roofline": {"bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
                           "frac": round(achieved / peak, 4),
