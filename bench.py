@@ -518,7 +518,7 @@ def main():
                      "timing": "CUDA events around 50 back-to-back napspmv_spmv_step launches on "
                                "the benchmark stream after the timed region; inside it the "
                                "overlapped engine runs the same rows as a local and a remote "
-                               "launch (shares in profiles/overlap_engine_128cube_launches.md)",
+                               "launch",
                      "algorithmic_bytes": B_spmv, "launch_ms": round(spmv_ms, 5)},
         "step_roofline": {"bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
                           "frac": round(achieved / peak, 4),
