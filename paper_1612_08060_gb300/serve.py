@@ -276,6 +276,10 @@ def compare(count=512, n_lo=1e3, n_hi=2e5, seed=1239, load=0.8, device=None, swe
     t0 = time.perf_counter()
     plain_sat = Server(max_active=1, cache=cache, device=device).run(base, realtime=False)
     sat_s = time.perf_counter() - t0
+    # saturated throughput of the batching server: every request queued at once
+    t0 = time.perf_counter()
+    Server(max_active=64, cache=cache, device=device).run(base, realtime=False)
+    batched_sat_s = time.perf_counter() - t0
 
     def at(ld):
         rate = ld * count / sat_s
@@ -294,7 +298,8 @@ def compare(count=512, n_lo=1e3, n_hi=2e5, seed=1239, load=0.8, device=None, swe
 
     main = at(load)
     out = {"requests": count, "n_range": [n_lo, n_hi], "rate_hz": main["rate_hz"],
-           "plan_build_s": build_s, "plain_saturated_rps": count / sat_s, "mix": main["mix"],
+           "plan_build_s": build_s, "plain_saturated_rps": count / sat_s,
+           "batched_saturated_rps": count / batched_sat_s, "mix": main["mix"],
            "tolerance": "SpMV FP64 <= 1e-13 normwise; CG-IR ||b - Ax|| / ||b|| <= 1e-10",
            "batched": main["batched"], "plain": main["plain"]}
     if sweep:
