@@ -7,8 +7,9 @@
  * simulated process and node living on one GPU:
  *
  *   - the rows of the N x N matrix A are split into n_p contiguous blocks, one
- *     per simulated process (Sec. 2, Eq. R), and the processes are grouped ppn
- *     per simulated node, process r being (r mod ppn, floor(r / ppn));
+ *     per simulated process (Sec. 2, Eq. R; or strided, row i on process
+ *     i mod n_p, with NAPSPMV_PARTITION_STRIDED), and the processes are grouped
+ *     ppn per simulated node, process r being (r mod ppn, floor(r / ppn));
  *   - each process's rows are split into on-process, on-node and off-node
  *     column blocks (Sec. 2, Eqs. on_proc, on_node, off_node);
  *   - napspmv_plan builds, on the GPU, the standard communication plan
@@ -19,7 +20,10 @@
  *     algorithm as a device gather or copy in HBM (on_node -> on_node and
  *     on_node -> off_node local exchanges, packing of g_send, the inter-node
  *     transfer g_send -> g_recv, the off_node -> on_node forwarding) and the
- *     three-block SpMV, for all simulated processes in one persistent launch.
+ *     three-block SpMV, for all simulated processes at once: by default as a
+ *     CUDA graph of kernels in which the on_process part of the SpMV overlaps
+ *     the message steps (NAPSPMV_ENGINE_OVERLAP), or in one persistent launch
+ *     (NAPSPMV_ENGINE_FUSED).
  *
  * Conventions for every call:
  *   - Return value: NAPSPMV_OK (0) or a negative NAPSPMV_ERR_* code; the
@@ -32,7 +36,8 @@
  *     plan (or one workspace) must not overlap on the host, and applies that
  *     use the same workspace must be ordered on one stream.
  *   - Limits: N < 2^30, nnz < 2^31, and every receive buffer < 2^30 values.
- *     Larger inputs are rejected with NAPSPMV_ERR_UNSUPPORTED.
+ *     Larger inputs are rejected with NAPSPMV_ERR_UNSUPPORTED, as are the
+ *     engine / plan combinations documented with the plan flags.
  *   - There is no CPU fallback: without a usable CUDA device every call that
  *     needs one fails with NAPSPMV_ERR_CUDA.
  */
@@ -53,7 +58,8 @@ extern "C" {
 #define NAPSPMV_ERR_CUDA (-3)        /* a CUDA runtime call failed               */
 #define NAPSPMV_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up       */
 #define NAPSPMV_ERR_STATE (-5)       /* call not valid in the object's state     */
-#define NAPSPMV_ERR_UNSUPPORTED (-6) /* size beyond the limits above             */
+#define NAPSPMV_ERR_UNSUPPORTED (-6) /* size beyond the limits above, or an
+                                        engine a plan's flags exclude            */
 
 /* ------------------------------------------------------------ memory kinds */
 #define NAPSPMV_HOST 0
