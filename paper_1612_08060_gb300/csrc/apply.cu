@@ -216,6 +216,16 @@ __device__ __forceinline__ double f2d_exact(float f)
     return f2d_rare(f);
 }
 
+// Value loads of the message steps: each value is read once per apply, so no
+// L2 priority is asked for (an evict-last mark on every message buffer crowds
+// out x, which the SpMV gathers keep resident).  Fused engine: plain loads.
+template <bool INKERNEL, class T>
+__device__ __forceinline__ T ldm(const T *p)
+{
+    if (INKERNEL) return *p;
+    return __ldg(p);
+}
+
 // Batched element loop over [b, e): U independent index loads, then U
 // independent data loads, then U stores, per thread and step.
 // WAIT: the index arrays are constant plan data, so the index loads are issued
@@ -480,7 +490,7 @@ __device__ __forceinline__ void tile_compute(const TileStage &st, const XT *x, c
         if (MODE == kRemote && i < nr && lane == 0) acc = ld_partial_f64(y + r0 + i);
         if (i < nr) {
             const int s = st.rows[r0 - rb + i] - kb, e = st.rows[r0 - rb + i + 1] - kb;
-#pragma unroll 8
+#pragma unroll 4
             for (int k = s + lane; k < e; k += V)
                 acc = entry_add<F32>(acc, st.val, val32, k, load_x<INKERNEL>(st.col[k], x, bll, bnl));
         }
@@ -713,7 +723,7 @@ __device__ __noinline__ void step_gather(T *dst, const T *src, const int32_t *id
     const uint64_t pol = policy_evict_first();
     batched<U, T, WAIT>(
         b, e, tid, [&](int k) { return (uint32_t)ld_stream_hint_s32(idx + k, pol); },
-        [&](int, uint32_t j) { return ldx<INKERNEL>(src + j); },
+        [&](int, uint32_t j) { return ldm<INKERNEL>(src + j); },
         [&](int k, uint32_t, T v) { dst[k] = v; });
 }
 template <bool INKERNEL, int U, class T = double, bool WAIT = false>
@@ -724,7 +734,7 @@ __device__ __noinline__ void step_pack(T *gsend, const T *x, const T *lbuf, cons
     batched<U, T, WAIT>(
         b, e, tid, [&](int k) { return ld_stream_hint_u32(src + k, pol); },
         [&](int, uint32_t u) {
-            return (u & kFromLbuf) ? ldx<INKERNEL>(lbuf + (u & ~kFromLbuf)) : ldx<INKERNEL>(x + u);
+            return (u & kFromLbuf) ? ldm<INKERNEL>(lbuf + (u & ~kFromLbuf)) : ldm<INKERNEL>(x + u);
         },
         [&](int k, uint32_t, T v) { gsend[k] = v; });
 }
@@ -735,7 +745,7 @@ __device__ __noinline__ void step_transfer(T *grecv, const T *gsend, const int32
     const uint64_t pol = policy_evict_first();
     batched<U, T, WAIT>(
         b, e, tid, [&](int k) { return (uint32_t)ld_stream_hint_s32(dst + k, pol); },
-        [&](int k, uint32_t) { return ldx<INKERNEL>(gsend + k); },
+        [&](int k, uint32_t) { return ldm<INKERNEL>(gsend + k); },
         [&](int, uint32_t d, T v) { grecv[d] = v; });
 }
 
@@ -991,7 +1001,7 @@ __device__ __forceinline__ void tile_compute_halo(const TileStage &st, const voi
         if (i < nr && lane == 0) acc = ld_partial_f64(y + r0 + i);
         if (i < nr) {
             const int s = st.rows[r0 - rb + i] - kb, e = st.rows[r0 - rb + i + 1] - kb;
-#pragma unroll 8
+#pragma unroll 4
             for (int k = s + lane; k < e; k += V) {
                 const uint32_t c = st.col[k];
                 const int idx = (int)(c & kIndexMask);
@@ -1199,7 +1209,7 @@ __global__ void __launch_bounds__(NT, 4)
                     if (MODE == kRemote && i < nr && sub == 0) acc = ld_partial_f64(y + it.b + i);
                     if (i < nr) {
                         const int s0 = st.rows[it.b - rb + i] - kb, e0 = st.rows[it.b - rb + i + 1] - kb;
-#pragma unroll 8
+#pragma unroll 4
                         for (int k = s0 + sub; k < e0; k += V)
                             acc = entry_add<F32>(acc, st.val, val32, k,
                                                  load_x<false>(st.col[k], x, bll, bnl));
