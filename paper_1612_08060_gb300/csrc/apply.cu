@@ -216,6 +216,32 @@ __device__ __forceinline__ double f2d_exact(float f)
     return f2d_rare(f);
 }
 
+// binary64 -> binary32, rounded to nearest with ties to even (IEEE 754), for a
+// result that is a normal binary32 number: the exponent loses 896, the 52-bit
+// fraction keeps its top 23 bits, and the 29 dropped bits decide the rounding
+// (above half, or exactly half with an odd last kept bit, adds one; a carry out
+// of the fraction moves into the exponent, and past the largest finite value
+// gives infinity, as the rounding rule requires).  Integer operations only;
+// zero, results below the binary32 normal range, overflow, infinities and NaNs
+// take the conversion instruction.
+__device__ __noinline__ float d2f_rare(double d)
+{
+    return __double2float_rn(d);  // a call, so that the common path does not execute it predicated
+}
+__device__ __forceinline__ float d2f_rn(double d)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned e = (unsigned)(u >> 52) & 0x7ffu;
+    if (e - 897u <= 253u) {  // exponent field 897..1150: binary32 exponent 1..254
+        const unsigned hi = (unsigned)(u >> 29) & 0x7fffffu;
+        const unsigned rest = (unsigned)u & 0x1fffffffu;
+        unsigned f = ((e - 896u) << 23) | hi;
+        f += (rest > 0x10000000u || (rest == 0x10000000u && (hi & 1u))) ? 1u : 0u;
+        return __uint_as_float(f | ((unsigned)(u >> 32) & 0x80000000u));
+    }
+    return d2f_rare(d);
+}
+
 // Value loads of the message steps: each value is read once per apply, so no
 // L2 priority is asked for (an evict-last mark on every message buffer crowds
 // out x, which the SpMV gathers keep resident).  Fused engine: plain loads.
@@ -279,7 +305,7 @@ __device__ __forceinline__ double f32_product(float a, XT xv)
 {
     float xf;
     if constexpr (sizeof(XT) == 4) xf = xv;
-    else xf = __double2float_rn(xv);
+    else xf = d2f_rn(xv);
     return f2d_exact(__fmul_rn(a, xf));
 }
 template <bool F32, class XT>
@@ -505,7 +531,7 @@ __device__ __forceinline__ void tile_compute(const TileStage &st, const XT *x, c
             } else {
                 const double r = apply_scale(acc, sc);
                 y[r0 + i] = r;
-                if (y32) y32[r0 + i] = __double2float_rn(r);
+                if (y32) y32[r0 + i] = d2f_rn(r);
             }
         }
     }
@@ -539,7 +565,7 @@ __device__ void row_direct(const Csr3 &A, const XT *x, const XT *bll, const XT *
             } else {
                 const double r = apply_scale(t, sc);
                 y[i] = r;
-                if (y32) y32[i] = __double2float_rn(r);
+                if (y32) y32[i] = d2f_rn(r);
             }
         }
         __syncthreads();
@@ -913,7 +939,7 @@ __global__ void __launch_bounds__(NT) k_to_f32(const double *v, float *v32, int6
     griddep_wait();
     if (*(volatile const int *)err) return;
     for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
-        v32[i] = __double2float_rn(ld_stream_f64(v + i));
+        v32[i] = d2f_rn(ld_stream_f64(v + i));
     griddep_done();
 }
 template <int V, bool F32, int MODE = kFull>
@@ -1017,7 +1043,7 @@ __device__ __forceinline__ void tile_compute_halo(const TileStage &st, const voi
         if (i < nr && lane == 0) {
             const double r = apply_scale(acc, sc);
             y[r0 + i] = r;
-            if (y32) y32[r0 + i] = __double2float_rn(r);
+            if (y32) y32[r0 + i] = d2f_rn(r);
         }
     }
 }
@@ -1121,7 +1147,7 @@ __global__ void __launch_bounds__(NT)
                     for (int w2 = 0; w2 < NT / 32; w2++) t2 = __dadd_rn(t2, red[w2]);
                     const double res = apply_scale(t2, sc);
                     y[r] = res;
-                    if (y32) y32[r] = __double2float_rn(res);
+                    if (y32) y32[r] = d2f_rn(res);
                 }
                 __syncthreads();
             }
@@ -1225,7 +1251,7 @@ __global__ void __launch_bounds__(NT, 4)
                         } else {
                             const double r = apply_scale(acc, sc);
                             y[it.b + i] = r;
-                            if (y32) y32[it.b + i] = __double2float_rn(r);
+                            if (y32) y32[it.b + i] = d2f_rn(r);
                         }
                     }
                 }
@@ -1251,7 +1277,7 @@ __global__ void __launch_bounds__(NT, 4)
                     } else {
                         const double res = apply_scale(acc, sc);
                         y[r] = res;
-                        if (y32) y32[r] = __double2float_rn(res);
+                        if (y32) y32[r] = d2f_rn(res);
                     }
                 }
             }

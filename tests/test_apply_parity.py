@@ -336,6 +336,29 @@ def test_unaligned_output_vector(reps):
     assert np.linalg.norm(aligned - ref) <= 1e-13 * reps * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("eng", ENGINES)
+def test_fp32_narrowing_rounding_cases(eng):
+    """x rounded to FP32 before the product: exact halfway cases (ties to
+    even, up and down), cases just off a tie, the carry into the exponent, the
+    largest finite FP32 value and its halfway point to infinity, the smallest
+    normal FP32 exponent and values just below it, compared bit for bit with
+    the oracle's C conversion through rows of one entry of value 1."""
+    t = 2.0 ** -24
+    x = np.array([1 + t, 1 + 3 * t, 1 + t + 2.0 ** -40, 1 + t - 2.0 ** -40, -(1 + t),
+                  -(1 + 3 * t), 2 - t, 2 - t / 2, 3.4028234663852886e38,
+                  3.4028235677973366e38, 3.4028235677973362e38, 2.0 ** -126 * (1 + t),
+                  2.0 ** -126 * (1 + 3 * t), 2.0 ** -126 - 2.0 ** -150, 2.0 ** -149 * 1.5,
+                  0.1, -1.0 / 3.0, 7.0e-39])
+    n = len(x)
+    A = I.CSR(np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n))
+    w = run(gpu_plan(A, 6, 2), x, precision=nap.PREC_F32, **eng)
+    with np.errstate(all="ignore"):
+        ref = O.spmv_f32(A.row_ptr, A.col, np.ones(n, np.float32), x)
+    assert np.array_equal(w.view(np.uint64), ref.view(np.uint64)), (w, ref)
+    with np.errstate(all="ignore"):
+        assert np.array_equal(ref, x.astype(np.float32).astype(np.float64))
+
+
 def test_host_entry_point():
     A = I.poisson2d(40)
     v = I.vector(A.n, 4)
