@@ -343,6 +343,11 @@ int napspmv_cg(napspmv_plan_t *P, const double *b, double *x, double rtol, int32
  * [4] latest r.r, [5] b.b.  Not in the paper: the batched form of the
  * request server; each slot's arithmetic does not depend on the others in
  * the call (fixed per-slot reduction order). */
+/* Slots (and served SpMV requests) whose matrix holds at least this many
+ * stored entries are applied on their own with the phased engine: there one
+ * product costs less than its share of a fused-engine launch. */
+#define NAPSPMV_SOLO_NNZ (1ll << 19)
+
 typedef struct {
     napspmv_plan_t *plan;
     napspmv_ws_t *ws;
@@ -357,10 +362,13 @@ typedef struct {
 int napspmv_cg_batch_init(int32_t count, const napspmv_cg_slot *slots, int32_t precision,
                           int32_t x_is_zero, void *stream);
 
-/* `iters` CG iterations for every slot: q = A p (one batched apply for all
- * slots), alpha = r.r / p.q, x += alpha p, r -= alpha q, beta = r.r_new /
- * r.r, p = r + beta p.  Asynchronous; the caller reads scal[0] to decide
- * convergence. */
+/* `iters` CG iterations for every slot: q = A p, alpha = r.r / p.q,
+ * x += alpha p, r -= alpha q, beta = r.r_new / r.r, p = r + beta p.
+ * Asynchronous; the caller reads scal[0] to decide convergence.
+ * The products q = A p (and r = b - A x of napspmv_cg_batch_init): slots whose
+ * matrix holds at least NAPSPMV_SOLO_NNZ stored entries are applied one by one
+ * on the phased engine, the others together in one fused-engine launch.  The
+ * choice depends on the slot's own matrix, not on the rest of the batch. */
 int napspmv_cg_batch_iterate(int32_t count, const napspmv_cg_slot *slots, int32_t precision,
                              int32_t iters, void *stream);
 

@@ -22,6 +22,7 @@ PREC_F64, PREC_F32 = 0, 1
 ENGINE_DEFAULT, ENGINE_FUSED, ENGINE_PHASED, ENGINE_OVERLAP = 0, 1, 2, 3
 PIPELINE_CTA, PIPELINE_WARP = 1, 2
 HALO_ON, HALO_OFF = 1, 2
+SOLO_NNZ = 1 << 19  # NAPSPMV_SOLO_NNZ
 (LIST_STD, LIST_NODE, LIST_INTER, LIST_J0, LIST_J1, LIST_J2, LIST_BLL, LIST_BNL, LIST_LBUF,
  LIST_TU, LIST_SPLIT) = range(11)
 

@@ -10,7 +10,11 @@ differing size.  The server:
 * every step launches one batched fused apply for all SpMV requests, one batched
   CG-residual step (FP64 values) for the solves entering an outer iteration, and
   ``iters_per_step`` batched CG iterations (FP32 values) for the solves in their
-  inner loop, so the work of all admitted requests overlaps on the device;
+  inner loop, so the work of all admitted requests overlaps on the device.
+  Requests on a matrix of at least ``SOLO_NNZ`` stored entries take their
+  products on the phased engine, one call each, where a product costs less than
+  its share of the fused launch (the batched CG calls route their slots the
+  same way);
 * reads every solve's scalars with one device-to-host copy per step, retires
   finished requests and stamps their latency (completion - arrival).
 
@@ -39,6 +43,7 @@ class Matrix:
         t0 = time.perf_counter()
         self.key = key
         self.n = A.n
+        self.solo = A.nnz >= nap.SOLO_NNZ
         self.plan = nap.napspmv_plan(A.row_ptr, A.col, A.val, n_p, ppn, nap.F32_VALUES)
         self.build_s = time.perf_counter() - t0
         st = nap.napspmv_plan_stats(self.plan)
@@ -76,6 +81,7 @@ class Server:
         self.max_outer, self.max_inner = max_outer, max_inner
         self.keep = keep_results
         self.stream = torch.cuda.Stream(self.dev)
+        self.solo_opts = nap.make_opts(engine=nap.ENGINE_PHASED)
         # plans may be shared between servers (a warm cache): their bytes are
         # then counted by whoever built them
         self.cache: "collections.OrderedDict[str, Matrix]" = (
@@ -169,7 +175,11 @@ class Server:
         inner = [r for r in active if r.state == "inner"]
         self.batch_sizes.append(len(active))
         with torch.cuda.stream(s):
-            for grp in self._chunks(spmv):
+            for r in spmv:
+                if r.m.solo:
+                    nap.napspmv_apply_batch([r.m.plan], [r.v], [r.w], [1], opts=self.solo_opts,
+                                            ws=[r.ws], stream=s)
+            for grp in self._chunks([r for r in spmv if not r.m.solo]):
                 nap.napspmv_apply_batch([r.m.plan for r in grp], [r.v for r in grp],
                                         [r.w for r in grp], [1] * len(grp),
                                         ws=[r.ws for r in grp], stream=s)

@@ -85,3 +85,24 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(nap, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         nap.lib()
+
+
+def test_binding_constants_match_the_header():
+    """The Python names of the flag, engine and threshold values carry the
+    header's numbers."""
+    from paper_1612_08060_gb300 import napspmv as nap
+    text = open(HEADER).read()
+    defs = {}
+    for name, val in re.findall(r"#define (NAPSPMV_\w+) \(?([0-9a-fx]+[ul]*(?: << \d+)?)\)?", text):
+        val = re.sub(r"(?<=\d)[ul]+", "", val)
+        defs[name] = eval(val)  # literal integers and shifts only
+    pairs = {"F32_VALUES": "NAPSPMV_F32_VALUES", "MAP_TEXT": "NAPSPMV_MAP_TEXT",
+             "PARTITION_STRIDED": "NAPSPMV_PARTITION_STRIDED",
+             "MAP_MAJORITY": "NAPSPMV_MAP_MAJORITY", "COMPOSED_GATHERS": "NAPSPMV_COMPOSED_GATHERS",
+             "ENGINE_FUSED": "NAPSPMV_ENGINE_FUSED", "ENGINE_PHASED": "NAPSPMV_ENGINE_PHASED",
+             "ENGINE_OVERLAP": "NAPSPMV_ENGINE_OVERLAP", "PIPELINE_CTA": "NAPSPMV_PIPELINE_CTA",
+             "PIPELINE_WARP": "NAPSPMV_PIPELINE_WARP", "HALO_ON": "NAPSPMV_HALO_ON",
+             "HALO_OFF": "NAPSPMV_HALO_OFF", "SOLO_NNZ": "NAPSPMV_SOLO_NNZ"}
+    for py, c in pairs.items():
+        assert c in defs, c
+        assert getattr(nap, py) == defs[c], (py, getattr(nap, py), defs[c])

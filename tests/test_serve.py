@@ -46,3 +46,32 @@ def test_memory_budget_admission():
     assert all(r.state == "done" for r in reqs)
     assert max(srv.batch_sizes) < len(specs)  # the budget held some requests back
     assert srv.mem_used <= srv.budget
+
+
+def test_solo_matrices_alone_equals_mix():
+    """Requests on matrices of at least SOLO_NNZ entries take the phased engine
+    (SpMV and batched CG alike), the rest share the fused launch; results stay
+    the same bits served alone or in a mix, and correct."""
+    from paper_1612_08060_gb300 import napspmv as nap, serve
+    shapes = [(3, 44, "cg"), (2, 330, "spmv"), (3, 44, "spmv"), (2, 40, "cg"), (3, 14, "spmv"),
+              (2, 90, "cg"), (2, 330, "cg")]
+    specs = []
+    for q, (dim, side, kind) in enumerate(shapes):
+        n = side ** dim
+        specs.append(dict(id=q, arrival=0.0002 * q, kind=kind, dim=dim, side=side, n=n,
+                          n_p=max(1, round(n / 2048)), ppn=16, seed=1000 + q))
+    big = [s for s in specs if _matrix(s).nnz >= nap.SOLO_NNZ]
+    assert {s["kind"] for s in big} == {"spmv", "cg"} and len(big) < len(specs)
+    mixed = serve.Server(max_active=64, keep_results=True).run(specs, realtime=True)
+    alone = serve.Server(max_active=1, keep_results=True).run(specs, realtime=False)
+    by_id = {r.id: r for r in alone}
+    for r in mixed:
+        assert np.array_equal(r.result, by_id[r.id].result), r.id
+        A = _matrix(r.spec)
+        rhs = I.vector(A.n, r.spec["seed"])
+        if r.kind == "spmv":
+            ref = O.spmv(A.row_ptr, A.col, A.val, rhs)
+            assert np.linalg.norm(r.result - ref) <= 1e-13 * np.linalg.norm(ref)
+        else:
+            res = rhs - O.spmv(A.row_ptr, A.col, A.val, r.result)
+            assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(rhs), r.id
