@@ -613,6 +613,13 @@ struct Job {
     double *w;
 };
 
+// A run of tickets that all belong to one dataflow level of one job.
+struct Seg {
+    long long t0;  // first ticket within one apply of every job
+    int32_t job;
+    int32_t item0;  // the job's item that t0 takes
+};
+
 template <int MAXJ>
 struct FusedParams {
     int32_t njobs;
@@ -622,8 +629,17 @@ struct FusedParams {
     long long total;
     long long timeout_ns;
     unsigned long long *ticket;
+    // Ticket order.  nseg == 0: the jobs one after another, each job's applies
+    // in turn.  nseg > 0 (a batch whose jobs chain equally many applies):
+    // apply by apply, and within one apply level by level across all jobs, so
+    // that the message steps of every job run before any CTA waits in a row
+    // tile.  Both orders are topological: an item only waits on earlier tickets.
+    int32_t nseg;
+    long long period;  // tickets per apply of all jobs (nseg > 0)
+    Seg seg[MAXJ > 1 ? 5 * MAXJ : 1];
     Job jobs[MAXJ];
 };
+static_assert(sizeof(FusedParams<64>) <= 32764, "kernel parameters are limited to 32,764 bytes");
 
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
 {
@@ -780,13 +796,30 @@ __device__ __forceinline__ bool staged_tile(const Item &it, int cap)
     return it.kind == kSpmv && it.k1 - it.k0 <= cap;
 }
 
+// Ticket t -> its job (returned), the apply k of that job and the item index.
 template <int MAXJ>
-__device__ __forceinline__ const Job &job_of(const FusedParams<MAXJ> &prm, long long t)
+__device__ __forceinline__ int locate(const FusedParams<MAXJ> &prm, long long t, int &k, int &idx)
 {
+    if (MAXJ > 1 && prm.nseg > 0) {
+        k = (int)(t / prm.period);
+        const long long r = t - (long long)k * prm.period;
+        int lo = 0, hi = prm.nseg - 1;  // the last run that starts at or before r
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prm.seg[mid].t0 <= r) lo = mid;
+            else hi = mid - 1;
+        }
+        idx = prm.seg[lo].item0 + (int)(r - prm.seg[lo].t0);
+        return prm.seg[lo].job;
+    }
     int ji = 0;
     if (MAXJ > 1)
         while (ji + 1 < prm.njobs && prm.jobs[ji + 1].tbase <= t) ji++;
-    return prm.jobs[MAXJ > 1 ? ji : 0];
+    const Job &J = prm.jobs[ji];
+    const long long tl = t - J.tbase;
+    k = (int)(tl / J.n_items);
+    idx = (int)(tl % J.n_items);
+    return ji;
 }
 
 template <int V, bool F32, int MAXJ>
@@ -805,8 +838,9 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
     if (tid == 0) {
         s_t = (long long)atomicAdd(prm.ticket, 1ull);
         if (s_t < prm.total) {
-            const Job &J = job_of(prm, s_t);
-            const Item it = J.items[(s_t - J.tbase) % J.n_items];
+            int k0, i0;
+            const Job &J = prm.jobs[locate(prm, s_t, k0, i0)];
+            const Item it = J.items[i0];
             if (staged_tile(it, cap))
                 tile_issue<F32>(J.A, tile_stage(smem, 0, cap, trows), it.b, it.e, it.k0, it.k1);
         }
@@ -815,18 +849,18 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
     for (;;) {
         const long long t = s_t;
         if (t >= prm.total) break;
-        const Job &J = job_of(prm, t);
-        const long long tl = t - J.tbase;
-        const int k = (int)(tl / J.n_items);
-        const Item it = J.items[tl % J.n_items];
+        int k, idx;
+        const Job &J = prm.jobs[locate(prm, t, k, idx)];
+        const Item it = J.items[idx];
         const int cur = seq & 1;
         if (tid == 0) {
             next = (long long)atomicAdd(prm.ticket, 1ull);
             // the matrix is read-only: the next tile's slices are fetched before
             // its dependencies are even checked
             if (next < prm.total) {
-                const Job &Jn = job_of(prm, next);
-                const Item itn = Jn.items[(next - Jn.tbase) % Jn.n_items];
+                int kn, in;
+                const Job &Jn = prm.jobs[locate(prm, next, kn, in)];
+                const Item itn = Jn.items[in];
                 if (staged_tile(itn, cap))
                     tile_issue<F32>(Jn.A, tile_stage(smem, cur ^ 1, cap, trows), itn.b, itn.e,
                                     itn.k0, itn.k1);
@@ -842,8 +876,9 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
             if (staged_tile(it, cap)) tile_wait(tile_stage(smem, cur, cap, trows), (phase >> cur) & 1, J.err);
             const long long nx = s_next;
             if (nx < prm.total) {
-                const Job &Jn = job_of(prm, nx);
-                if (staged_tile(Jn.items[(nx - Jn.tbase) % Jn.n_items], cap))
+                int kn, in;
+                const Job &Jn = prm.jobs[locate(prm, nx, kn, in)];
+                if (staged_tile(Jn.items[in], cap))
                     tile_wait(tile_stage(smem, cur ^ 1, cap, trows), (phase >> (cur ^ 1)) & 1,
                               J.err);
             }
@@ -1365,9 +1400,12 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
     for (int x = 0; x < nn; x++)
         for (int64_t b = P->node_lbuf[x]; b < P->node_lbuf[x + 1]; b += chunk)
             add(kGatherJ0, x, b, std::min<int64_t>(b + chunk, P->node_lbuf[x + 1]), 0, kC1);
+    int32_t lvl[6] = {0};
+    lvl[1] = (int32_t)items.size();
     for (int x = 0; x < nn; x++)
         for (int64_t b = P->node_gs[x]; b < P->node_gs[x + 1]; b += chunk)
             add(kPack, x, b, std::min<int64_t>(b + chunk, P->node_gs[x + 1]), 0, kC2);
+    lvl[2] = (int32_t)items.size();
     const std::vector<int64_t> &off = P->gs_msg_off;
     for (int x = 0; x < nn; x++)
         for (int64_t b = P->node_gs[x]; b < P->node_gs[x + 1]; b += chunk) {
@@ -1376,10 +1414,12 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
         }
     for (size_t m = 0; m + 1 < off.size(); m++)
         cnt[(size_t)kArr * nn + P->gs_msg_dstnode[m]] += (uint64_t)(off[m + 1] - off[m]);
+    lvl[3] = (int32_t)items.size();
     for (int x = 0; x < nn; x++)
         for (int64_t b = P->node_bnl[x]; b < P->node_bnl[x + 1]; b += chunk)
             add(kUnpack, x, b, std::min<int64_t>(b + chunk, P->node_bnl[x + 1]), 0, kC4);
     const int32_t spmv_first = (int32_t)items.size();
+    lvl[4] = spmv_first;
     const std::vector<int32_t> &rp = P->h_rowptr;
     for (int x = 0; x < nn; x++) {
         int64_t r = P->node_rows[x];
@@ -1513,6 +1553,8 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
     S.d_cnt = d_cnt;
     S.n_items = (int32_t)items.size();
     S.spmv_first = spmv_first;
+    lvl[5] = (int32_t)items.size();
+    std::copy(lvl, lvl + 6, S.lvl);
     S.chunk = chunk;
     S.tile_rows = tile_rows;
     S.tile_nnz = tile_nnz;
@@ -1630,6 +1672,26 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
         NAP_CUDA(cudaMemsetAsync(wi->ctr, 0, sizeof(unsigned long long) * ctr_count(plans[i]), s));
     }
     prm.total = total;
+    bool by_level = MAXJ > 1 && count > 1;
+    for (int i = 1; i < count; i++) by_level = by_level && reps[i] == reps[0];
+    if (by_level) {
+        long long acc = 0;
+        int ns = 0;
+        for (int L = 0; L < 5; L++)
+            for (int i = 0; i < count; i++) {
+                const int32_t *lv = plans[i]->items.lvl;
+                if (lv[L + 1] > lv[L]) {
+                    prm.seg[ns].t0 = acc;
+                    prm.seg[ns].job = i;
+                    prm.seg[ns].item0 = lv[L];
+                    ns++;
+                    acc += lv[L + 1] - lv[L];
+                }
+            }
+        prm.nseg = ns;
+        prm.period = acc;
+        prm.total = acc * reps[0];  // the same count as job after job
+    }
     prm.ticket = prm.jobs[0].ctr;
     auto fn = FusedKernelTable<MAXJ>::get(o.vec, f32);
     const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows);

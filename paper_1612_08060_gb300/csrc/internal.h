@@ -62,6 +62,9 @@ struct ItemSet {
     int32_t chunk = 0, tile_rows = 0, tile_nnz = 0;
     int32_t n_items = 0;
     int32_t spmv_first = 0;  // items [spmv_first, n_items) are the row tiles
+    // items [lvl[L], lvl[L+1]) are level L of the dataflow: gathers, packs,
+    // transfers, unpacks, row tiles
+    int32_t lvl[6] = {};
     Item *d_tilesL = nullptr, *d_tilesR = nullptr;  // tiles of the split parts
     int32_t n_tilesL = 0, n_tilesR = 0;
     // remote tiles cut at process boundaries (Item::msg = process), for the

@@ -39,6 +39,32 @@ def test_batch_equals_alone():
         assert np.linalg.norm(got - ref) <= 1e-13 * r * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("reps,prec", [(1, nap.PREC_F64), (3, nap.PREC_F64), (1, nap.PREC_F32)])
+def test_batch_level_order_equals_alone(reps, prec):
+    """Jobs that chain equally many applies take their tickets level by level
+    across the batch (every job's message steps, then the row tiles); the bits
+    stay those of each apply alone."""
+    mats = [(I.poisson3d(24), 27, 4), (I.poisson2d(90), 40, 16), (I.poisson3d(13), 1, 1),
+            (I.aniso_q1(40), 64, 8), (I.random_pattern(500, 0.02, 7), 12, 3),
+            (I.poisson3d(20), 16, 16)]
+    plans = [nap.napspmv_plan(A.row_ptr, A.col, A.val, n_p, ppn, flags=nap.F32_VALUES)
+             for (A, n_p, ppn) in mats]
+    vs = [torch.from_numpy(I.vector(A.n, 30 + k)).cuda() for k, (A, _, _) in enumerate(mats)]
+    outs = [torch.full_like(v, float("nan")) for v in vs]
+    opts = nap.make_opts(engine=nap.ENGINE_FUSED, precision=prec)
+    nap.napspmv_apply_batch(plans, vs, outs, [reps] * len(mats), [0.125] * len(mats), opts=opts)
+    for k, (A, _, _) in enumerate(mats):
+        assert nap.napspmv_status(plans[k]) == 0
+        alone = torch.empty_like(vs[k])
+        nap.napspmv_apply_ex(plans[k], vs[k], alone, reps, 0.125, opts)
+        torch.cuda.synchronize()
+        assert torch.equal(alone, outs[k]), k
+        if prec == nap.PREC_F64:
+            ref = oracle_chain(A, vs[k].cpu().numpy(), reps, 0.125)
+            got = outs[k].cpu().numpy()
+            assert np.linalg.norm(got - ref) <= 1e-13 * reps * np.linalg.norm(ref)
+
+
 def test_batch_rejects_shared_workspace():
     A = I.poisson2d(10)
     p = gpu_plan(A, 4, 2)
