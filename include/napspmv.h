@@ -246,7 +246,10 @@ int napspmv_apply_host(napspmv_plan_t *P, const double *v_host, double *w_host, 
  * request server.  ws[i] may be NULL only if no other entry uses the same
  * plan's own workspace.  count <= 64.  Fused engine (count = 1 runs as
  * napspmv_apply_ex with the given options), so with count > 1 plans built
- * with NAPSPMV_PARTITION_STRIDED give ERR_UNSUPPORTED. */
+ * with NAPSPMV_PARTITION_STRIDED give ERR_UNSUPPORTED.  Errors stay per
+ * entry: an entry whose wait times out sets its workspace's error flag
+ * (napspmv_ws_status) and its remaining work is skipped; the other entries
+ * complete. */
 int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const *ws,
                         const double *const *v, double *const *w, const int32_t *reps,
                         const double *scale, const napspmv_opts *opts, void *stream);

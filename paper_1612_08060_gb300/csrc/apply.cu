@@ -872,17 +872,31 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
         }
         __syncthreads();
         if (!s_ok) {
-            // leave no bulk copy in flight: drain the stages issued for t and next
-            if (staged_tile(it, cap)) tile_wait(tile_stage(smem, cur, cap, trows), (phase >> cur) & 1, J.err);
-            const long long nx = s_next;
-            if (nx < prm.total) {
-                int kn, in;
-                const Job &Jn = prm.jobs[locate(prm, nx, kn, in)];
-                if (staged_tile(Jn.items[in], cap))
-                    tile_wait(tile_stage(smem, cur ^ 1, cap, trows), (phase >> (cur ^ 1)) & 1,
-                              J.err);
+            // The item's job has failed (its error flag is set): skip the item
+            // without signalling, so that the job's later items skip too, and go
+            // on with the next ticket, so that the other jobs of a batch finish.
+            // The stage of t is drained before it is reused; should even that copy
+            // not land, the stage of next is drained as well and the CTA stops.
+            bool drained = true;
+            if (staged_tile(it, cap)) {
+                drained = tile_wait(tile_stage(smem, cur, cap, trows), (phase >> cur) & 1, J.err);
+                phase ^= 1u << cur;
             }
-            break;
+            if (!__syncthreads_and(drained)) {
+                const long long nx = s_next;
+                if (nx < prm.total) {
+                    int kn, in;
+                    const Job &Jn = prm.jobs[locate(prm, nx, kn, in)];
+                    if (staged_tile(Jn.items[in], cap))
+                        tile_wait(tile_stage(smem, cur ^ 1, cap, trows), (phase >> (cur ^ 1)) & 1,
+                                  J.err);
+                }
+                break;
+            }
+            seq++;
+            if (tid == 0) s_t = next;
+            __syncthreads();
+            continue;
         }
         const double *x = (k == 0) ? J.v : (((J.reps - k) & 1) == 0 ? J.w : J.xtmp);
         double *y = (((J.reps - 1 - k) & 1) == 0) ? J.w : J.xtmp;
