@@ -931,6 +931,18 @@ __global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedPa
     }
 }
 
+// The dependency counters of every job of a batched launch zeroed in one
+// launch (one block per job) instead of one memset per job.
+struct CtrZero {
+    unsigned long long *p[64];
+    int32_t n[64];
+};
+__global__ void __launch_bounds__(NT) k_zero_ctrs(const __grid_constant__ CtrZero Z)
+{
+    unsigned long long *p = Z.p[blockIdx.x];
+    for (int k = threadIdx.x; k < Z.n[blockIdx.x]; k += NT) p[k] = 0ull;
+}
+
 // --------------------------------------------------------- phased engine
 template <class T>
 __global__ void __launch_bounds__(NT)
@@ -1677,13 +1689,23 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
     prm.tile_rows = o.tile_rows;
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
     long long total = 0;
+    CtrZero Z;
+    memset(&Z, 0, sizeof(Z));
     for (int i = 0; i < count; i++) {
         napspmv_ws_t *wi = ws && ws[i] ? ws[i] : plans[i]->ws;
         prm.jobs[i] = make_job(plans[i], wi, v[i], w[i], reps[i], scale ? scale[i] : 1.0, f32);
         prm.jobs[i].tbase = total;
         total += (long long)prm.jobs[i].n_items * reps[i];
         wi->buf_f32 = 0;  // this engine's receive buffers hold FP64 values in both modes
-        NAP_CUDA(cudaMemsetAsync(wi->ctr, 0, sizeof(unsigned long long) * ctr_count(plans[i]), s));
+        Z.p[i] = wi->ctr;
+        Z.n[i] = (int32_t)ctr_count(plans[i]);
+    }
+    if (count == 1) {
+        NAP_CUDA(cudaMemsetAsync(Z.p[0], 0, sizeof(unsigned long long) * Z.n[0], s));
+    } else {
+        k_zero_ctrs<<<count, NT, 0, s>>>(Z);
+        NAP_CUDA(cudaGetLastError());
+        count_launch(1);
     }
     prm.total = total;
     bool by_level = MAXJ > 1 && count > 1;
