@@ -10,6 +10,8 @@ the equation behind each one and the readings of the points the paper leaves
 open.
 """
 import ctypes as C
+import os
+
 import numpy as np
 
 from . import build as _build
@@ -50,7 +52,9 @@ _PF32 = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 def lib():
     global _lib
     if _lib is None:
-        l = C.CDLL(_build.build())
+        # NAPSPMV_ORACLE_LIB: a copy of the oracle with a planted mistake, loaded
+        # by the test that checks the pins catch it (never set otherwise)
+        l = C.CDLL(os.environ.get("NAPSPMV_ORACLE_LIB") or _build.build())
         l.orc_row_start.restype = C.c_int64
         l.orc_row_start.argtypes = [C.c_int64, C.c_int64, C.c_int64]
         l.orc_owner.restype = C.c_int64
