@@ -249,7 +249,12 @@ int napspmv_apply_host(napspmv_plan_t *P, const double *v_host, double *w_host, 
  * with NAPSPMV_PARTITION_STRIDED give ERR_UNSUPPORTED.  Errors stay per
  * entry: an entry whose wait times out sets its workspace's error flag
  * (napspmv_ws_status) and its remaining work is skipped; the other entries
- * complete. */
+ * complete.  Options: the fields of `opts` left 0 (or opts NULL) take the
+ * defaults of plans[0], for every entry (one kernel, one lane count per row).
+ * Each entry's result is bit-identical to napspmv_apply_ex of its plan with
+ * those resolved options; with its own plan's defaults instead (another lane
+ * count where rows average more than 16 entries), an FP64 row sum may round
+ * in another order. */
 int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const *ws,
                         const double *const *v, double *const *w, const int32_t *reps,
                         const double *scale, const napspmv_opts *opts, void *stream);
@@ -345,7 +350,9 @@ int napspmv_cg(napspmv_plan_t *P, const double *b, double *x, double rtol, int32
  * device doubles of scalars: [0] r.r, [1] p.q, [2] alpha, [3] beta,
  * [4] latest r.r, [5] b.b.  Not in the paper: the batched form of the
  * request server; each slot's arithmetic does not depend on the others in
- * the call (fixed per-slot reduction order). */
+ * the call (fixed per-slot reduction order), given that the slots sharing the
+ * fused launch have plans with the same default options (the launch takes the
+ * first such slot's). */
 /* Slots (and served SpMV requests) whose matrix holds at least this many
  * stored entries are applied on their own with the phased engine: there one
  * product costs less than its share of a fused-engine launch. */

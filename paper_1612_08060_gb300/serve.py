@@ -20,7 +20,9 @@ differing size.  The server:
 
 Each request's arithmetic is independent of what else is in flight (fixed
 per-row and per-slot reduction orders), so a request served alone and in a mix
-gives the same bits.  ``max_active=1`` is the plain per-request loop (same
+gives the same bits.  This holds while the matrices that share a fused launch
+have the same default launch options, as all of the served Poisson matrices do
+(one lane per row): a fused launch takes its first plan's options.  ``max_active=1`` is the plain per-request loop (same
 kernels, same plan cache, one request at a time in arrival order).
 
 PyTorch provides device memory and the stream; all compute is in libnapspmv.
