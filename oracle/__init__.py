@@ -24,6 +24,7 @@ LIST_NAMES = ["STD", "NODE", "INTER", "J0", "J1", "J2", "BLL", "BNL", "LBUF"]
 MAP_TEXT = 2
 STRIDED = 4  # row i on rank i mod n_p (the strided partition of Sec. 5)
 MAP_MAJORITY = 8  # node pairs mapped to the processes owning / using most of E(n,m)
+MAP_SPLIT = 16  # a node with fewer partner nodes than processes is split over them
 
 STAT_NAMES = [
     "std_msgs", "std_vals", "std_intra_msgs", "std_intra_vals", "std_inter_msgs",

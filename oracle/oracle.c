@@ -42,7 +42,22 @@
  *     ASCENDING, ties by n ascending, and give the k-th to local process
  *     P(m)-1-(k mod P(m)), where P(x) is the number of ranks on node x.
  *     Flag ORC_MAP_TEXT sorts the receiving side by |E| descending, as the
- *     prose states.  A node is never split over several processes.
+ *     prose states.  Without ORC_MAP_SPLIT a node is never split over several
+ *     processes (the tables do not split).
+ *   - Flag ORC_MAP_SPLIT (the text after Eq. U: when N(n) holds fewer nodes
+ *     than n has processes, a node is mapped to several processes so that
+ *     all of them communicate).  On a node x with P(x) processes and K < P(x)
+ *     partner nodes (sorted as above), partner k gets a contiguous group of
+ *     floor(P/K) + (k < P mod K) processes: on the sending side counted from
+ *     process 0 upwards, on the receiving side from process P-1 downwards
+ *     (the first partner gets the highest group).  With K >= P(x) each group
+ *     is the single process of the default rule.  For the pair (n,m) with
+ *     sending group S and receiving group R (ascending), E(n,m) in ascending
+ *     j is cut into c = max(|S|,|R|) contiguous pieces, piece i holding
+ *     positions floor(i e / c) .. floor((i+1) e / c) - 1 (e = |E(n,m)|);
+ *     piece i is sent by S[i mod |S|] to R[i mod |R|]; empty pieces send
+ *     nothing.  G and I follow from these messages; T/U report the first
+ *     process of each group.  Excludes ORC_MAP_MAJORITY.
  *   - Flag ORC_MAP_MAJORITY (the alternative the text names after Eq. U):
  *     node pair (n,m) is sent by the process of n that owns the most values
  *     of E(n,m), and received by the process of m whose rows use the most
@@ -72,6 +87,7 @@
 #define ORC_MAP_TEXT 2 /* same bit as the library's flag, chosen independently */
 #define ORC_STRIDED 4  /* row i belongs to rank i mod n_p (Sec. 5's strided partition) */
 #define ORC_MAP_MAJORITY 8 /* the majority mapping named after Eq. U (see orc_plan_build) */
+#define ORC_MAP_SPLIT 16   /* node splitting when a node has fewer partners than processes */
 
 enum { L_STD = 0, L_NODE, L_INTER, L_J0, L_J1, L_J2, L_BLL, L_BNL, L_LBUF, L_COUNT };
 
@@ -284,7 +300,7 @@ int orc_plan_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t
     int rc = ORC_OK;
     *out = NULL;
     if (np < 1 || np > n || ppn < 1) return ORC_ERR_ARG;
-    if ((flags & ORC_MAP_MAJORITY) && (flags & ORC_MAP_TEXT)) return ORC_ERR_ARG;
+    if ((flags & ORC_MAP_MAJORITY) && (flags & (ORC_MAP_TEXT | ORC_MAP_SPLIT))) return ORC_ERR_ARG;
     rc = check_csr(n, nnz, row_ptr, col);
     if (rc) return rc;
 
@@ -344,12 +360,18 @@ int orc_plan_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t
         int64_t m = N->m;
         P->send_proc = (int64_t *)calloc((size_t)(m ? m : 1), sizeof(int64_t));
         P->recv_proc = (int64_t *)calloc((size_t)(m ? m : 1), sizeof(int64_t));
+        /* group sizes (1 unless the pair's node is split, ORC_MAP_SPLIT) */
+        int64_t *send_cnt = (int64_t *)calloc((size_t)(m ? m : 1), sizeof(int64_t));
+        int64_t *recv_cnt = (int64_t *)calloc((size_t)(m ? m : 1), sizeof(int64_t));
         tu_entry *e = (tu_entry *)calloc((size_t)(m ? m : 1), sizeof(tu_entry));
-        if (!P->send_proc || !P->recv_proc || !e) {
+        if (!P->send_proc || !P->recv_proc || !send_cnt || !recv_cnt || !e) {
             free(e);
+            free(send_cnt);
+            free(recv_cnt);
             rc = ORC_ERR_OOM;
             goto done;
         }
+        for (int64_t k = 0; k < m; k++) send_cnt[k] = recv_cnt[k] = 1;
         if (flags & ORC_MAP_MAJORITY) {
             /* per node pair, count the values of E(n,m) each process of n owns
              * and the values each process of m uses, and take the largest */
@@ -387,7 +409,19 @@ int orc_plan_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t
                         c++;
                     }
                 qsort(e, (size_t)c, sizeof(tu_entry), tu_desc);
-                for (int64_t k = 0; k < c; k++) P->send_proc[e[k].msg] = k % procs_on_node(P, nd);
+                int64_t pn = procs_on_node(P, nd);
+                if ((flags & ORC_MAP_SPLIT) && c < pn) {
+                    /* partner k: processes first .. first + size - 1, upwards */
+                    int64_t first = 0;
+                    for (int64_t k = 0; k < c; k++) {
+                        int64_t size = pn / c + (k < pn % c ? 1 : 0);
+                        P->send_proc[e[k].msg] = first;
+                        send_cnt[e[k].msg] = size;
+                        first += size;
+                    }
+                } else {
+                    for (int64_t k = 0; k < c; k++) P->send_proc[e[k].msg] = k % pn;
+                }
                 /* receiving side: the nodes that have nd in their N(.) */
                 c = 0;
                 for (int64_t k = 0; k < m; k++)
@@ -398,21 +432,45 @@ int orc_plan_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t
                         c++;
                     }
                 qsort(e, (size_t)c, sizeof(tu_entry), (flags & ORC_MAP_TEXT) ? tu_desc : tu_asc);
-                for (int64_t k = 0; k < c; k++)
-                    P->recv_proc[e[k].msg] = procs_on_node(P, nd) - 1 - (k % procs_on_node(P, nd));
+                if ((flags & ORC_MAP_SPLIT) && c < pn) {
+                    /* partner k: the group below the earlier partners' groups,
+                     * counted down from process pn - 1 */
+                    int64_t top = pn;
+                    for (int64_t k = 0; k < c; k++) {
+                        int64_t size = pn / c + (k < pn % c ? 1 : 0);
+                        P->recv_proc[e[k].msg] = top - size;
+                        recv_cnt[e[k].msg] = size;
+                        top -= size;
+                    }
+                } else {
+                    for (int64_t k = 0; k < c; k++) P->recv_proc[e[k].msg] = pn - 1 - (k % pn);
+                }
             }
         }
         free(e);
 
         /* G and I (Eqs. G, IGset_send): one message per node pair, from the
          * process T assigns on n to the process U assigns on m, carrying
-         * E(n,m). */
+         * E(n,m); with ORC_MAP_SPLIT, piece i of E(n,m) from the i-th process
+         * of the sending group to the i-th of the receiving group (cyclic). */
         for (int64_t k = 0; k < m; k++) {
-            int64_t s = N->src[k] * ppn + P->send_proc[k];
-            int64_t d = N->dst[k] * ppn + P->recv_proc[k];
-            for (int64_t q = N->ptr[k]; q < N->ptr[k + 1]; q++)
-                if (tpush(&inter, s, d, N->idx[q])) { rc = ORC_ERR_OOM; goto done; }
+            int64_t ns = send_cnt[k], nr = recv_cnt[k];
+            int64_t c = ns > nr ? ns : nr, len = N->ptr[k + 1] - N->ptr[k];
+            for (int64_t i = 0; i < c; i++) {
+                int64_t s = N->src[k] * ppn + P->send_proc[k] + i % ns;
+                int64_t d = N->dst[k] * ppn + P->recv_proc[k] + i % nr;
+                int64_t lo = i * len / c, hi = (i + 1) * len / c;
+                for (int64_t q = N->ptr[k] + lo; q < N->ptr[k] + hi; q++)
+                    if (tpush(&inter, s, d, N->idx[q])) {
+                        free(send_cnt);
+                        free(recv_cnt);
+                        rc = ORC_ERR_OOM;
+                        goto done;
+                    }
+            }
         }
+        free(send_cnt);
+        free(recv_cnt);
         tset(&inter);
         if ((rc = tlist(&inter, &P->l[L_INTER]))) goto done;
     }

@@ -23,7 +23,23 @@ def partition(n, n_p, strided=False):
     return R
 
 
-def brute_plan(n, rows, n_p, ppn, map_text=False, strided=False, majority=False):
+def _groups(P, K, from_top):
+    """Node splitting: the processes (local ids) of a node with P processes given
+    to its K partners in order, floor(P/K) + (k < P mod K) each; counted up from
+    process 0, or down from process P-1 (from_top)."""
+    out, lo, hi = [], 0, P
+    for k in range(K):
+        size = P // K + (1 if k < P % K else 0)
+        if from_top:
+            out.append(list(range(hi - size, hi)))
+            hi -= size
+        else:
+            out.append(list(range(lo, lo + size)))
+            lo += size
+    return out
+
+
+def brute_plan(n, rows, n_p, ppn, map_text=False, strided=False, majority=False, split=False):
     """rows[i] = set of stored columns of row i.  Returns a dict of dicts:
     STD/J0/J1/J2/INTER: {(src, dst): sorted tuple}; NODE: {(n, m): tuple};
     BLL/BNL/LBUF: {rank: tuple}; T, U: {rank: set of nodes}; G: {rank: set};
@@ -83,16 +99,58 @@ def brute_plan(n, rows, n_p, ppn, map_text=False, strided=False, majority=False)
             recvs.sort(key=lambda x: (len(NODE[(x, a)]), x))
         for k, x in enumerate(recvs):
             U[node_ranks[a][P - 1 - (k % P)]].add(x)
-    out["T"], out["U"] = T, U
     # Eq. G and Eq. I
     G = {r: set() for r in range(n_p)}
     INTER = {}
-    for r in range(n_p):
-        for q in range(n_p):
-            m, x = q // ppn, r // ppn
-            if m in T[r] and x in U[q]:
-                G[r].add(q)
-                INTER[(r, q)] = NODE[(x, m)]
+    if split:
+        # the text after Eq. U: a node with fewer partners than processes maps
+        # each partner to a group of its processes; E(a, m) is cut into
+        # max(|S|, |R|) contiguous pieces, piece i from S[i mod |S|] to
+        # R[i mod |R|]
+        T = {r: set() for r in range(n_p)}
+        U = {r: set() for r in range(n_p)}
+        sgrp, rgrp = {}, {}
+        for a in range(nn):
+            P = len(node_ranks[a])
+            sends = sorted([m for (x, m) in NODE if x == a],
+                           key=lambda m: (-len(NODE[(a, m)]), m))
+            if len(sends) < P:
+                for m, g in zip(sends, _groups(P, len(sends), False)):
+                    sgrp[(a, m)] = [node_ranks[a][p] for p in g]
+            else:
+                for k, m in enumerate(sends):
+                    sgrp[(a, m)] = [node_ranks[a][k % P]]
+            recvs = [x for (x, m) in NODE if m == a]
+            if map_text:
+                recvs.sort(key=lambda x: (-len(NODE[(x, a)]), x))
+            else:
+                recvs.sort(key=lambda x: (len(NODE[(x, a)]), x))
+            if len(recvs) < P:
+                for x, g in zip(recvs, _groups(P, len(recvs), True)):
+                    rgrp[(x, a)] = [node_ranks[a][p] for p in g]
+            else:
+                for k, x in enumerate(recvs):
+                    rgrp[(x, a)] = [node_ranks[a][P - 1 - (k % P)]]
+        for (x, m), E in NODE.items():
+            S, Rg = sgrp[(x, m)], rgrp[(x, m)]
+            for r in S:
+                T[r].add(m)
+            for q in Rg:
+                U[q].add(x)
+            c, e = max(len(S), len(Rg)), len(E)
+            for i in range(c):
+                piece = E[i * e // c:(i + 1) * e // c]
+                if piece:
+                    G[S[i % len(S)]].add(Rg[i % len(Rg)])
+                    INTER[(S[i % len(S)], Rg[i % len(Rg)])] = tuple(piece)
+    else:
+        for r in range(n_p):
+            for q in range(n_p):
+                m, x = q // ppn, r // ppn
+                if m in T[r] and x in U[q]:
+                    G[r].add(q)
+                    INTER[(r, q)] = NODE[(x, m)]
+    out["T"], out["U"] = T, U
     out["G"], out["INTER"] = G, INTER
     # Eq. IL0: on_node -> off_node
     J0 = {}

@@ -206,3 +206,80 @@ def test_majority_with_map_text_rejected():
     with pytest.raises(ValueError):
         O.OraclePlan(A.row_ptr, A.col, 4, 2, flags=O.MAP_MAJORITY | O.MAP_TEXT)
 
+
+
+# ------------------------------------------------------------------ node splitting
+@pytest.mark.parametrize("n,dens,seed,n_p,ppn", CASES[::2])
+@pytest.mark.parametrize("text", [False, True])
+def test_split_matches_set_definitions(n, dens, seed, n_p, ppn, text):
+    """Node splitting (the text after Eq. U): the oracle's plans against the
+    literal set evaluation of the same reading."""
+    A = random_pattern(n, dens, seed)
+    flags = O.MAP_SPLIT | (O.MAP_TEXT if text else 0)
+    plan = O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=flags)
+    b = brute_plan(n, _rows(A), n_p, ppn, map_text=text, split=True)
+    for name, kind in LISTS:
+        assert plan.list_dict(kind) == b[name], name
+    for name, kind in LAYOUTS:
+        got = {s: idx for (s, d), idx in plan.list_dict(kind).items()}
+        assert got == b[name], name
+    v = np.random.default_rng(seed).uniform(-1, 1, n)
+    w = plan.napspmv(A.row_ptr, A.col, A.val, v)
+    ref = A.to_dense() @ v
+    assert np.all(np.abs(w - ref) <= 4 * np.finfo(float).eps * (np.abs(A.to_dense()) @ np.abs(v)))
+
+
+def test_split_worked_example_by_hand():
+    """The paper's worked example under node splitting, derived by hand from the
+    reading: node 2 sends only to node 0 and node 1 receives only from node 0,
+    so both are split over their two processes; the other pairs keep the
+    tables' processes.  Seven inter-node messages of one value each, and every
+    process sends and receives."""
+    import golden_example as G
+    ex = G.load()
+    n = len(ex["rows"])
+    rp = np.zeros(n + 1, np.int64)
+    cols = []
+    for i in range(n):
+        c = sorted(ex["rows"][i])
+        cols += c
+        rp[i + 1] = rp[i] + len(c)
+    plan = O.OraclePlan(rp, np.array(cols, np.int32), ex["np"], ex["ppn"], flags=O.MAP_SPLIT)
+    # ranks: (p, n) = n * 2 + p
+    assert plan.list_dict(O.INTER) == {(0, 2): (0,), (0, 3): (1,), (1, 5): (0,), (2, 1): (3,),
+                                       (3, 4): (2,), (4, 0): (4,), (5, 0): (5,)}
+    assert plan.list_dict(O.J0) == {(0, 1): (0,), (1, 0): (1,), (3, 2): (3,), (2, 3): (2,)}
+    assert plan.list_dict(O.J1) == {(0, 1): (4,), (1, 0): (3,), (2, 3): (0,), (5, 4): (0,)}
+    sp, rpn = plan.tu()  # node pairs (0,1) (0,2) (1,0) (1,2) (2,0): first process of each group
+    assert list(sp) == [0, 1, 0, 1, 0] and list(rpn) == [0, 1, 1, 0, 0]
+    st = plan.stats()
+    assert st["nap_inter_msgs"] == 7 and st["nap_inter_vals"] == 7
+
+
+def test_split_every_process_communicates():
+    """2D 5-point 16 x 16, one grid line per process, four processes per node,
+    four nodes: every node has fewer partner nodes (one or two) than processes,
+    so under node splitting every process sends and receives at least one
+    inter-node message; unsplit, only one process per node pair does.  The
+    values moved between nodes are the same (a grid line per node pair), cut
+    into pieces of 4 (a one-partner node, four ways) or 8 values (two ways)."""
+    from paper_1612_08060_gb300.inputs import poisson2d
+    A = poisson2d(16)
+    split = O.OraclePlan(A.row_ptr, A.col, 16, 4, flags=O.MAP_SPLIT)
+    plain = O.OraclePlan(A.row_ptr, A.col, 16, 4)
+    I = split.list_dict(O.INTER)
+    assert {s for (s, d) in I} == set(range(16)) == {d for (s, d) in I}
+    assert len({s for (s, d) in plain.list_dict(O.INTER)}) == 6
+    assert sorted({len(v) for v in I.values()}) == [4, 8]
+    # pieces of a pair are contiguous and cover E(n, m) exactly
+    E = split.list_dict(O.NODE)
+    for (a, m), vals in E.items():
+        got = sorted(j for (s, d), idx in I.items() if s // 4 == a and d // 4 == m for j in idx)
+        assert got == list(vals)
+    assert split.stats()["nap_inter_vals"] == plain.stats()["nap_inter_vals"] == 6 * 16
+
+
+def test_split_with_majority_rejected():
+    A = random_pattern(12, 0.3, 1)
+    with pytest.raises(ValueError):
+        O.OraclePlan(A.row_ptr, A.col, 4, 2, flags=O.MAP_MAJORITY | O.MAP_SPLIT)

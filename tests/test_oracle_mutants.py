@@ -35,8 +35,8 @@ MUTANTS = [
      "qsort(e, (size_t)c, sizeof(tu_entry), tu_asc);"),
     # U: receive processes counted from the front instead of from ppn - 1
     ("recv_order_not_reversed",
-     "P->recv_proc[e[k].msg] = procs_on_node(P, nd) - 1 - (k % procs_on_node(P, nd));",
-     "P->recv_proc[e[k].msg] = k % procs_on_node(P, nd);"),
+     "for (int64_t k = 0; k < c; k++) P->recv_proc[e[k].msg] = pn - 1 - (k % pn);",
+     "for (int64_t k = 0; k < c; k++) P->recv_proc[e[k].msg] = k % pn;"),
     # the prose mapping rule and the tables' rule exchanged
     ("text_rule_swapped", "(flags & ORC_MAP_TEXT) ? tu_desc : tu_asc",
      "(flags & ORC_MAP_TEXT) ? tu_asc : tu_desc"),
@@ -61,6 +61,17 @@ MUTANTS = [
     # the strided partition shifted by one row
     ("strided_shifted", "if (P->flags & ORC_STRIDED) return j % P->np;",
      "if (P->flags & ORC_STRIDED) return (j + 1) % P->np;"),
+    # node splitting: the larger groups given to the last partners, not the first
+    ("split_extra_processes_last",
+     "int64_t size = pn / c + (k < pn % c ? 1 : 0);\n                        P->send_proc[e[k].msg] = first;",
+     "int64_t size = pn / c + (k >= c - pn % c ? 1 : 0);\n                        P->send_proc[e[k].msg] = first;"),
+    # node splitting: pieces received by the receiving group in reverse order
+    ("split_pieces_reversed", "int64_t d = N->dst[k] * ppn + P->recv_proc[k] + i % nr;",
+     "int64_t d = N->dst[k] * ppn + P->recv_proc[k] + (nr - 1 - i % nr);"),
+    # node splitting: pieces cut by a rounded-up size instead of floor(i e / c)
+    ("split_ceil_pieces", "int64_t lo = i * len / c, hi = (i + 1) * len / c;",
+     "int64_t z = (len + c - 1) / c, lo = i * z < len ? i * z : len,\n"
+     "                        hi = (i + 1) * z < len ? (i + 1) * z : len;"),
     # CG: the search direction's update with the wrong sign
     ("cg_beta_sign", "p[i] = r[i] + beta * p[i];", "p[i] = r[i] - beta * p[i];"),
 ]
