@@ -86,6 +86,19 @@ extern "C" {
  * sender through the on->off step and those the receiver only forwards.
  * Excludes NAPSPMV_MAP_TEXT (ERR_ARG). */
 #define NAPSPMV_MAP_MAJORITY (1u << 3)
+/* Node splitting, the mapping the text after Eq. U describes for a node with
+ * fewer partner nodes than processes: each partner gets a group of the node's
+ * processes so that all of them communicate.  On a node with P processes and
+ * K < P partners (ordered as by the default rule), partner k gets
+ * floor(P/K) + (k < P mod K) consecutive processes, counted up from process 0
+ * on the sending side and down from process P-1 on the receiving side.  For
+ * the pair (n,m) with sending group S and receiving group R, E(n,m) (ascending
+ * j) is cut into max(|S|,|R|) contiguous pieces, piece i holding positions
+ * floor(i e / c) .. floor((i+1) e / c) - 1, sent by S[i mod |S|] to
+ * R[i mod |R|]; empty pieces are no message.  Nodes with at least P partners
+ * map as without the flag.  NAPSPMV_LIST_TU then reports the first process of
+ * each group.  Excludes NAPSPMV_MAP_MAJORITY (ERR_ARG). */
+#define NAPSPMV_MAP_SPLIT (1u << 5)
 /* Composed gathers, an ablation with no counterpart in the paper: each
  * process's receive buffers are gathered straight from v (b_{l->l} as in the
  * on->on step, b_{nl->l} from the owners' values), skipping the on->off
@@ -113,6 +126,12 @@ extern "C" {
 
 #define NAPSPMV_PIPELINE_CTA 1
 #define NAPSPMV_PIPELINE_WARP 2
+/* Sliced rows: every process's rows sorted by length and packed 32 to a
+ * chunk, column-major, one lane per row (no shared-memory stage; the chunk's
+ * columns and values are read coalesced straight from global memory).  Each
+ * row is summed in its stored order, so the bits are those of vec = 1; the
+ * vec field is ignored.  Phased and overlapped engines. */
+#define NAPSPMV_PIPELINE_SELL 3
 
 #define NAPSPMV_HALO_ON 1  /* overlapped engine: stage each process's receive
                               buffers in shared memory for its remote rows when
@@ -153,10 +172,11 @@ typedef struct {
     int32_t stages;      /* shared-memory stages of the phased SpMV pipeline
                             (2..4; the fused engine always uses 2)             */
     int32_t pipeline;    /* SpMV tiles of the phased / overlapped engines:
-                            NAPSPMV_PIPELINE_CTA (a CTA per tile) or
+                            NAPSPMV_PIPELINE_CTA (a CTA per tile),
                             NAPSPMV_PIPELINE_WARP (each warp its own stages and
-                            tiles of tile_rows / 8 rows, tile_nnz / 8 entries);
-                            a CTA takes a contiguous run of tiles either way */
+                            tiles of tile_rows / 8 rows, tile_nnz / 8 entries;
+                            a CTA takes a contiguous run of tiles either way)
+                            or NAPSPMV_PIPELINE_SELL (sliced rows, above)     */
     int32_t halo;        /* NAPSPMV_HALO_ON / _OFF (overlapped engine)         */
     int32_t timeout_ms;  /* limit of every device-side wait                    */
     int32_t debug_stall; /* test hook (fused engine): 1 makes the first work
@@ -200,8 +220,8 @@ typedef struct {
  *   A      CSR (host or device memory), see napspmv_csr.
  *   n_p    1 <= n_p <= N;  ppn >= 1 (the last node may hold fewer processes).
  *   flags  NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT or NAPSPMV_MAP_MAJORITY |
- *          NAPSPMV_PARTITION_STRIDED | NAPSPMV_COMPOSED_GATHERS; other bits:
- *          ERR_ARG.
+ *          NAPSPMV_MAP_SPLIT (not with MAJORITY) | NAPSPMV_PARTITION_STRIDED |
+ *          NAPSPMV_COMPOSED_GATHERS; other bits: ERR_ARG.
  *   out    receives the plan; the caller frees it with napspmv_plan_destroy.
  * Runs on the current device and synchronises it.  Errors: ERR_ARG for a
  * malformed CSR or bad n_p / ppn, ERR_UNSUPPORTED beyond the size limits,
@@ -268,13 +288,17 @@ int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_
  *   - Receive buffers, the chain vector and dependency counters come from one
  *     fixed array of 2^20 doubles (8 MiB) that this library reserves on every
  *     device that loads it, until the process exits.  Plans needing more
- *     (counters + b_{l->l} + b_{l->nl} + 2 g_send + b_{nl->l} + N values)
- *     are rejected with NAPSPMV_ERR_UNSUPPORTED and a message giving both sizes.
+ *     (see below) are rejected with NAPSPMV_ERR_UNSUPPORTED and a message
+ *     giving both sizes.
  *   - Every call shares that array and it keeps the last call's contents;
  *     the counters are cleared by each call.  Calls that overlap on the GPU
  *     (on different streams, or on different plans) race on it: order them.
  *   - The first call on a device looks the array's device address up (with
  *     that device current); make that first call before any stream capture.
+ *     The address is cached for the life of the process: it does not survive
+ *     cudaDeviceReset on that device.
+ *   - Scratch needed: counters + b_{l->l} + b_{l->nl} + 2 g_send + b_{nl->l}
+ *     values, plus N for the chain vector when reps > 1.
  *   - Uses the fused engine with the plan's current work items and FP64
  *     values (strided plans: ERR_UNSUPPORTED); device-side timeouts are
  *     reported by napspmv_status(P). */

@@ -339,29 +339,6 @@ __device__ __forceinline__ double apply_scale(double acc, const Scale sc)
     return __dmul_rn(sc.s, acc);
 }
 
-__device__ __forceinline__ uint4 ld_stream_v4u32(const uint32_t *p)
-{
-    uint4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-        : "l"(p));
-    return v;
-}
-__device__ __forceinline__ double2 ld_stream_v2f64(const double *p)
-{
-    double2 v;
-    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ float4 ld_stream_v4f32(const float *p)
-{
-    float4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-        : "l"(p));
-    return v;
-}
-
 // ------------------------------------------- TMA-staged three-block SpMV
 // A row tile's slices of the row pointer, column and value arrays are brought
 // into shared memory by bulk asynchronous copies (cp.async.bulk, completion
@@ -593,54 +570,7 @@ __device__ __forceinline__ void tile_smem_init(unsigned char *base, int ns)
     __syncthreads();
 }
 
-// ---------------------------------------------------------- fused engine
-struct Job {
-    const Item *items;
-    int32_t n_items;
-    int32_t reps;
-    Scale scale;
-    long long tbase;  // first ticket of this job in the launch
-    Csr3 A;
-    const int32_t *bll_j, *lbuf_j, *xfer_dst, *unp_src;
-    const uint32_t *pack_src;
-    const int32_t *msg_off, *msg_dstnode;
-    const uint64_t *cnt;  // [kNumCounters][nn] per-apply increments
-    int32_t nn;
-    double *bll, *lbuf, *gsend, *grecv, *bnl, *xtmp;
-    unsigned long long *ctr;  // [0] ticket, then [kNumCounters][nn], then one spare
-    int *err;
-    const double *v;
-    double *w;
-};
-
-// A run of tickets that all belong to one dataflow level of one job.
-struct Seg {
-    long long t0;  // first ticket within one apply of every job
-    int32_t job;
-    int32_t item0;  // the job's item that t0 takes
-};
-
-template <int MAXJ>
-struct FusedParams {
-    int32_t njobs;
-    int32_t stall;
-    int32_t cap;        // tile capacity in stored entries (shared-memory stage)
-    int32_t tile_rows;  // tile capacity in rows
-    long long total;
-    long long timeout_ns;
-    unsigned long long *ticket;
-    // Ticket order.  nseg == 0: the jobs one after another, each job's applies
-    // in turn.  nseg > 0 (a batch whose jobs chain equally many applies):
-    // apply by apply, and within one apply level by level across all jobs, so
-    // that the message steps of every job run before any CTA waits in a row
-    // tile.  Both orders are topological: an item only waits on earlier tickets.
-    int32_t nseg;
-    long long period;  // tickets per apply of all jobs (nseg > 0)
-    Seg seg[MAXJ > 1 ? 5 * MAXJ : 1];
-    Job jobs[MAXJ];
-};
-static_assert(sizeof(FusedParams<64>) <= 32764, "kernel parameters are limited to 32,764 bytes");
-
+// ------------------------------------------------- device-side waits
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
 {
     unsigned long long v;
@@ -665,94 +595,6 @@ __device__ __forceinline__ bool wait_ge(const unsigned long long *p, unsigned lo
             atomicCAS(err, 0, 1);
             return false;
         }
-    }
-}
-
-struct Cond {
-    const unsigned long long *p;
-    unsigned long long t;
-};
-// All conditions: first one round of independent loads; only if one is not
-// yet met, spin on it.  Ends with the acquire fence that orders every later
-// load of this thread (and, through the CTA barrier, of the CTA) after the
-// producers' writes.
-__device__ __forceinline__ bool wait_all(const Cond *c, int n, int *err, long long tmo)
-{
-    unsigned long long v[4];
-#pragma unroll
-    for (int i = 0; i < 4; i++) v[i] = (i < n && c[i].t) ? ld_relaxed(c[i].p) : 0ull;
-    bool ok = true;
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-        if (i < n && v[i] < c[i].t) ok = false;
-    if (!ok)
-        for (int i = 0; i < n; i++)
-            if (!wait_ge(c[i].p, c[i].t, err, tmo)) return false;
-    fence_acq_rel();
-    return true;
-}
-
-__device__ __noinline__ bool item_deps(const Job &J, const Item &it, int k, long long tmo, bool stall)
-{
-    auto C = [&](int c, int node) { return J.ctr + 1 + c * J.nn + node; };
-    auto N = [&](int c, int node) { return (unsigned long long)J.cnt[c * J.nn + node]; };
-    const unsigned long long kk = k, k1 = k + 1;
-    const int n = it.node;
-    if (stall && !wait_ge(J.ctr + 1 + kNumCounters * J.nn, 1, J.err, tmo)) return false;
-    Cond c[4];
-    int m = 0;
-    switch (it.kind) {
-    case kGatherJ2:
-    case kGatherJ0:
-        // x_k rows of node n written; previous readers of b_{l->l}, b_{l->nl} done
-        c[m++] = {C(kC5, n), kk * N(kC5, n)};
-        c[m++] = {C(kC2, n), kk * N(kC2, n)};
-        break;
-    case kPack:
-        c[m++] = {C(kC1, n), k1 * N(kC1, n)};
-        c[m++] = {C(kC5, n), kk * N(kC5, n)};
-        c[m++] = {C(kC3, n), kk * N(kC3, n)};
-        break;
-    case kTransfer:
-        c[m++] = {C(kC2, n), k1 * N(kC2, n)};
-        if (k > 0) {
-            // previous readers of the destination nodes' g_recv slots done
-            for (int q = it.msg; J.msg_off[q] < it.e; q++) {
-                const int dn = J.msg_dstnode[q];
-                if (!wait_ge(C(kC4, dn), kk * N(kC4, dn), J.err, tmo)) return false;
-            }
-        }
-        break;
-    case kUnpack:
-        c[m++] = {C(kArr, n), k1 * N(kArr, n)};
-        c[m++] = {C(kC5, n), kk * N(kC5, n)};
-        break;
-    default:  // kSpmv
-        c[m++] = {C(kC1, n), k1 * N(kC1, n)};
-        c[m++] = {C(kC4, n), k1 * N(kC4, n)};
-        c[m++] = {C(kC5, n), kk * N(kC5, n)};
-        c[m++] = {C(kC2, n), kk * N(kC2, n)};
-        break;
-    }
-    return wait_all(c, m, J.err, tmo);
-}
-
-__device__ __noinline__ void item_signal(const Job &J, const Item &it)
-{
-    auto C = [&](int c, int node) { return J.ctr + 1 + c * J.nn + node; };
-    switch (it.kind) {
-    case kGatherJ2:
-    case kGatherJ0: atomicAdd(C(kC1, it.node), 1ull); break;
-    case kPack: atomicAdd(C(kC2, it.node), 1ull); break;
-    case kTransfer:
-        for (int m = it.msg; J.msg_off[m] < it.e; m++) {
-            const int lo = max(it.b, J.msg_off[m]), hi = min(it.e, J.msg_off[m + 1]);
-            if (hi > lo) atomicAdd(C(kArr, J.msg_dstnode[m]), (unsigned long long)(hi - lo));
-        }
-        atomicAdd(C(kC3, it.node), 1ull);
-        break;
-    case kUnpack: atomicAdd(C(kC4, it.node), 1ull); break;
-    default: atomicAdd(C(kC5, it.node), 1ull); break;
     }
 }
 
@@ -794,141 +636,6 @@ __device__ __noinline__ void step_transfer(T *grecv, const T *gsend, const int32
 __device__ __forceinline__ bool staged_tile(const Item &it, int cap)
 {
     return it.kind == kSpmv && it.k1 - it.k0 <= cap;
-}
-
-// Ticket t -> its job (returned), the apply k of that job and the item index.
-template <int MAXJ>
-__device__ __forceinline__ int locate(const FusedParams<MAXJ> &prm, long long t, int &k, int &idx)
-{
-    if (MAXJ > 1 && prm.nseg > 0) {
-        k = (int)(t / prm.period);
-        const long long r = t - (long long)k * prm.period;
-        int lo = 0, hi = prm.nseg - 1;  // the last run that starts at or before r
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (prm.seg[mid].t0 <= r) lo = mid;
-            else hi = mid - 1;
-        }
-        idx = prm.seg[lo].item0 + (int)(r - prm.seg[lo].t0);
-        return prm.seg[lo].job;
-    }
-    int ji = 0;
-    if (MAXJ > 1)
-        while (ji + 1 < prm.njobs && prm.jobs[ji + 1].tbase <= t) ji++;
-    const Job &J = prm.jobs[ji];
-    const long long tl = t - J.tbase;
-    k = (int)(tl / J.n_items);
-    idx = (int)(tl % J.n_items);
-    return ji;
-}
-
-template <int V, bool F32, int MAXJ>
-__global__ void __launch_bounds__(NT, 5) k_fused(const __grid_constant__ FusedParams<MAXJ> prm)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_t, s_next;
-    __shared__ int s_ok;
-    const int tid = threadIdx.x;
-    const int cap = prm.cap, trows = prm.tile_rows;
-    tile_smem_init(smem, 2);
-    double *red = tile_red(smem, cap, trows, 2);
-    uint32_t phase = 0;  // per-stage mbarrier parity, identical in every thread
-    int seq = 0;         // items taken by this CTA; item seq uses stage seq & 1
-    long long next = 0;
-    if (tid == 0) {
-        s_t = (long long)atomicAdd(prm.ticket, 1ull);
-        if (s_t < prm.total) {
-            int k0, i0;
-            const Job &J = prm.jobs[locate(prm, s_t, k0, i0)];
-            const Item it = J.items[i0];
-            if (staged_tile(it, cap))
-                tile_issue<F32>(J.A, tile_stage(smem, 0, cap, trows), it.b, it.e, it.k0, it.k1);
-        }
-    }
-    __syncthreads();
-    for (;;) {
-        const long long t = s_t;
-        if (t >= prm.total) break;
-        int k, idx;
-        const Job &J = prm.jobs[locate(prm, t, k, idx)];
-        const Item it = J.items[idx];
-        const int cur = seq & 1;
-        if (tid == 0) {
-            next = (long long)atomicAdd(prm.ticket, 1ull);
-            // the matrix is read-only: the next tile's slices are fetched before
-            // its dependencies are even checked
-            if (next < prm.total) {
-                int kn, in;
-                const Job &Jn = prm.jobs[locate(prm, next, kn, in)];
-                const Item itn = Jn.items[in];
-                if (staged_tile(itn, cap))
-                    tile_issue<F32>(Jn.A, tile_stage(smem, cur ^ 1, cap, trows), itn.b, itn.e,
-                                    itn.k0, itn.k1);
-            }
-            s_next = next;
-            // a sticky error (an earlier wait timed out) stops all work of the job
-            s_ok = !*(volatile int *)J.err &&
-                   item_deps(J, it, k, prm.timeout_ns, prm.stall && t == 0);
-        }
-        __syncthreads();
-        if (!s_ok) {
-            // The item's job has failed (its error flag is set): skip the item
-            // without signalling, so that the job's later items skip too, and go
-            // on with the next ticket, so that the other jobs of a batch finish.
-            // The stage of t is drained before it is reused; should even that copy
-            // not land, the stage of next is drained as well and the CTA stops.
-            bool drained = true;
-            if (staged_tile(it, cap)) {
-                drained = tile_wait(tile_stage(smem, cur, cap, trows), (phase >> cur) & 1, J.err);
-                phase ^= 1u << cur;
-            }
-            if (!__syncthreads_and(drained)) {
-                const long long nx = s_next;
-                if (nx < prm.total) {
-                    int kn, in;
-                    const Job &Jn = prm.jobs[locate(prm, nx, kn, in)];
-                    if (staged_tile(Jn.items[in], cap))
-                        tile_wait(tile_stage(smem, cur ^ 1, cap, trows), (phase >> (cur ^ 1)) & 1,
-                                  J.err);
-                }
-                break;
-            }
-            seq++;
-            if (tid == 0) s_t = next;
-            __syncthreads();
-            continue;
-        }
-        const double *x = (k == 0) ? J.v : (((J.reps - k) & 1) == 0 ? J.w : J.xtmp);
-        double *y = (((J.reps - 1 - k) & 1) == 0) ? J.w : J.xtmp;
-        switch (it.kind) {
-        case kGatherJ2: step_gather<true, 4>(J.bll, x, J.bll_j, it.b, it.e, tid); break;
-        case kGatherJ0: step_gather<true, 4>(J.lbuf, x, J.lbuf_j, it.b, it.e, tid); break;
-        case kPack: step_pack<true, 4>(J.gsend, x, J.lbuf, J.pack_src, it.b, it.e, tid); break;
-        case kTransfer: step_transfer<true, 4>(J.grecv, J.gsend, J.xfer_dst, it.b, it.e, tid); break;
-        case kUnpack: step_gather<true, 4>(J.bnl, J.grecv, J.unp_src, it.b, it.e, tid); break;
-        default:
-            if (staged_tile(it, cap)) {
-                const TileStage st = tile_stage(smem, cur, cap, trows);
-                const bool ok = tile_wait(st, (phase >> cur) & 1, J.err);
-                phase ^= 1u << cur;
-                if (ok)
-                    tile_compute<V, F32, true>(st, x, J.bll, J.bnl, y, nullptr, J.scale, it.b, it.e,
-                                               it.k0, tid);
-            } else {
-                row_direct<F32, true>(J.A, x, J.bll, J.bnl, y, nullptr, J.scale, it.b, it.e, red,
-                                      tid);
-            }
-            break;
-        }
-        seq++;
-        __syncthreads();
-        if (tid == 0) {
-            fence_acq_rel();  // the CTA's writes (ordered by the barrier) before the counters
-            item_signal(J, it);
-            s_t = next;
-        }
-        __syncthreads();
-    }
 }
 
 // The dependency counters of every job of a batched launch zeroed in one
@@ -1233,6 +940,35 @@ __host__ __device__ __forceinline__ int warp_smem_bytes(int capw, int rowsw, int
     return 16 * kMaxStages * WPB + WPB * ns * stage_layout(capw, rowsw, vb).bytes;
 }
 
+// One row summed by a whole warp straight from global memory (lanes stride the
+// row, fixed xor tree); REMOTE adds the partial to the warp's sum.
+template <bool F32, int MODE, bool INKERNEL = false, class XT>
+__device__ __forceinline__ void row_warp(const Csr3 &A, const XT *x, const XT *bll, const XT *bnl,
+                                         double *y, float *y32, const Scale sc, int r, int lane)
+{
+    const int s0 = ld_stream_s32(A.rowptr + r), e0 = ld_stream_s32(A.rowptr + r + 1);
+    double acc = 0.0;
+    for (int k = s0 + lane; k < e0; k += 32) {
+        const XT xv = load_x<INKERNEL>(ld_stream_u32(A.colenc + k), x, bll, bnl);
+        if constexpr (F32)
+            acc = __dadd_rn(acc, f32_product(ld_stream_f32(A.val32 + k), xv));
+        else
+            acc = fma(ld_stream_f64(A.val + k), xv, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) {
+        if (MODE == kRemote) acc = __dadd_rn(y[r], acc);
+        if (MODE == kLocal) {
+            y[r] = acc;
+        } else {
+            const double res = apply_scale(acc, sc);
+            y[r] = res;
+            if (y32) y32[r] = d2f_rn(res);
+        }
+    }
+}
+
 template <int V, bool F32, int MODE>
 __global__ void __launch_bounds__(NT, 4)
     k_spmv_w(Csr3 A, const void *xs, const void *blls, const void *bnls, double *y, float *y32,
@@ -1319,29 +1055,7 @@ __global__ void __launch_bounds__(NT, 4)
             }
         } else {
             // a row longer than a warp stage: the warp sums it from global memory
-            for (int r = it.b; r < it.e; r++) {
-                const int s0 = ld_stream_s32(A.rowptr + r), e0 = ld_stream_s32(A.rowptr + r + 1);
-                double acc = 0.0;
-                for (int k = s0 + lane; k < e0; k += 32) {
-                    const XT xv = load_x<false>(ld_stream_u32(A.colenc + k), x, bll, bnl);
-                    if constexpr (F32)
-                        acc = __dadd_rn(acc, f32_product(ld_stream_f32(A.val32 + k), xv));
-                    else
-                        acc = fma(ld_stream_f64(A.val + k), xv, acc);
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-                if (lane == 0) {
-                    if (MODE == kRemote) acc = __dadd_rn(y[r], acc);
-                    if (MODE == kLocal) {
-                        y[r] = acc;
-                    } else {
-                        const double res = apply_scale(acc, sc);
-                        y[r] = res;
-                        if (y32) y32[r] = d2f_rn(res);
-                    }
-                }
-            }
+            for (int r = it.b; r < it.e; r++) row_warp<F32, MODE>(A, x, bll, bnl, y, y32, sc, r, lane);
         }
         cur = cur + 1 == ns ? 0 : cur + 1;
         __syncwarp();
@@ -1349,24 +1063,366 @@ __global__ void __launch_bounds__(NT, 4)
     griddep_done();
 }
 
+// --------------------------------------------------- sliced-row SpMV
+// NAPSPMV_PIPELINE_SELL: one lane per row over chunks of up to 32 rows of
+// similar length stored column-major (slot first + i * lanes + lane).  A warp
+// reads a chunk's columns and values as consecutive slots, coalesced, straight
+// from global memory (no shared-memory stage, so occupancy is bounded by
+// registers only), and every lane of a DFMA carries an entry: the rows of a
+// chunk have similar counts.  Each row is summed in its stored order, one DFMA
+// per entry (FP32 mode: FP32 product, FP64 add): the bits of the one-lane CSR
+// kernels.  Chunks go to CTAs in contiguous runs (a CTA stays within a few
+// processes, whose receive buffers then stay in this SM's L1 / the L2), the
+// warps of a CTA interleaved.  Rows longer than kSellLong entries are summed
+// afterwards by whole warps from the CSR part.
+struct SellView {
+    const int2 *info;
+    const int32_t *perm;
+    const uint32_t *col;
+    const double *val;
+    const float *val32;
+    const int32_t *lrows;
+    Csr3 A;  // the same part as CSR (long rows)
+    int32_t nch, n_long;
+};
+
+__device__ __forceinline__ double ld_stream_hint_f64(const double *p, uint64_t pol)
+{
+    double v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_stream_hint_f32(const float *p, uint64_t pol)
+{
+    float v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// One chunk of a sliced-row part: lane `lane` sums the row of its slot in
+// the chunk (nothing if the chunk has fewer rows), U entries at a time: U
+// column loads and U value loads (coalesced across the warp, streamed with an
+// L2 evict-first mark), U gathers of x or the receive buffers, then U FMAs
+// in stored order.  INKERNEL: the sources are written earlier in the same
+// launch (the fused engine): coherent loads instead of the read-only path.
+template <bool F32, bool INKERNEL, int MODE, int U, class XT>
+__device__ __forceinline__ void sell_chunk(const SellView &S, int c, const XT *x, const XT *bll,
+                                           const XT *bnl, double *y, float *y32, const Scale sc,
+                                           int lane, uint64_t pol)
+{
+    using VT = typename std::conditional<F32, float, double>::type;
+    const int2 inf = S.info[c];
+    const int width = inf.y >> 6, nl = inf.y & 63;
+    if (lane >= nl) return;
+    const int row = S.perm[32 * c + lane];
+    double acc = MODE == kRemote ? ld_partial_f64(y + row) : 0.0;
+    const int64_t base = (int64_t)inf.x + lane;
+    for (int i = 0; i < width; i += U) {
+        uint32_t cc[U];
+        VT a[U];
+        XT xv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            cc[u] = i + u < width ? ld_stream_hint_u32(S.col + base + (int64_t)(i + u) * nl, pol)
+                                  : kSellPad;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t q = base + (int64_t)(i + u) * nl;
+            if constexpr (F32)
+                a[u] = cc[u] != kSellPad ? ld_stream_hint_f32(S.val32 + q, pol) : 0.0f;
+            else
+                a[u] = cc[u] != kSellPad ? ld_stream_hint_f64(S.val + q, pol) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            xv[u] = cc[u] != kSellPad ? load_x<INKERNEL>(cc[u], x, bll, bnl) : XT(0);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (cc[u] != kSellPad) {
+                if constexpr (F32) acc = __dadd_rn(acc, f32_product(a[u], xv[u]));
+                else acc = fma(a[u], xv[u], acc);
+            }
+        }
+    }
+    if (MODE == kLocal) {
+        st_partial_f64(y + row, acc);
+    } else {
+        const double r = apply_scale(acc, sc);
+        y[row] = r;
+        if (y32) y32[row] = d2f_rn(r);
+    }
+}
+
+// Chunks are handed out in groups of kSellGroup consecutive chunks (one per
+// warp of a CTA), group g to CTA g mod grid: every CTA sweeps the arrays
+// together with the others, so the pages in use at any time stay few.
+// Measured on the 2^23-row banded random workload (FP64): contiguous runs of
+// chunks per CTA, which spread ~900 CTAs over 3.4 GB of matrix and receive
+// buffers, took 1.42 ms; groups of 8 handed out this way, 0.70 ms.  Four
+// entries per step suit short rows (the stencils), eight longer ones.
+constexpr int kSellGroup = 8;
+
+template <bool F32, int MODE, int U>
+__global__ void __launch_bounds__(NT, U >= 8 ? 4 : 6)
+    k_spmv_s(SellView S, const void *xs, const void *blls, const void *bnls, double *y, float *y32,
+             Scale sc, int *err)
+{
+    using XT = typename std::conditional<F32, float, double>::type;
+    const XT *x = static_cast<const XT *>(xs), *bll = static_cast<const XT *>(blls),
+             *bnl = static_cast<const XT *>(bnls);
+    griddep_wait();
+    if (*(volatile const int *)err) return;  // sticky error: no work until cleared
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t pol = policy_evict_first();  // the matrix streams once per apply
+    const int ngroups = (S.nch + kSellGroup - 1) / kSellGroup;
+    for (int g = blockIdx.x; g < ngroups; g += gridDim.x)
+        for (int c = g * kSellGroup + warp; c < min(S.nch, (g + 1) * kSellGroup); c += WPB)
+            sell_chunk<F32, false, MODE, U>(S, c, x, bll, bnl, y, y32, sc, lane, pol);
+    // rows longer than kSellLong: a warp each
+    const int gw = blockIdx.x * WPB + warp, nw = gridDim.x * WPB;
+    for (int q = gw; q < S.n_long; q += nw) row_warp<F32, MODE>(S.A, x, bll, bnl, y, y32, sc, S.lrows[q], lane);
+    griddep_done();
+}
+
+// ---------------------------------------------------------- fused engine
+// One persistent, cooperative launch for every chained apply of one or more
+// independent jobs (a batch).  Each apply runs in five levels separated by
+// grid-wide barriers:
+//   level 0  the on_node -> on_node and on_node -> off_node gathers (Eqs. IL2,
+//            IL0); with composed gathers, both receive buffers from x
+//   level 1  packing of g_send (Eq. I) and the inter-node transfer g_send ->
+//            g_recv: the thread that packs element k also moves element k (it
+//            reads back the g_send value it wrote), so no barrier separates
+//            the two steps
+//   level 2  off_node -> on_node: unpack into b_{nl->l} (Eq. IL1)
+//   level 3  the three-block SpMV over the sliced rows (each row on_process,
+//            on_node, off_node in one FMA chain)
+// Splitting the rows into a local part overlapping levels 0-2 and a remote
+// part (the overlap Algorithm NAPSpMV allows) was measured slower on GB300:
+// the remote part's continuation of every row costs more than the local part
+// hides (3D 7-point 128^3: 152 against ~100 us per apply).  Within a level the
+// units of all jobs (message chunks of kFusedChunk elements, groups of
+// kSellGroup sliced-row chunks, groups of 8 long rows) are dealt to the CTAs
+// round robin: no ticket counter, no per-item dependency check, one barrier
+// per level.  Every CTA of the
+// cooperative launch is resident, so the barrier cannot wait on a CTA that
+// never runs; its wait is bounded all the same.
+constexpr int kFusedChunk = NT * 8;
+constexpr int kLevels = 4;
+
+struct FJob {
+    SellView F;                   // the whole matrix, sliced rows
+    const int32_t *src0, *src1;   // level-0 gathers: J2 / J0 (composed: BLL / BNL lists)
+    int32_t n0, n1;
+    const uint32_t *pack_src;
+    const int32_t *xfer_dst, *unp_src;
+    int32_t n_gs, n_bnl;
+    int32_t composed, reps;
+    Scale scale;
+    double *bll, *lbuf, *gsend, *grecv, *bnl, *xtmp;
+    int *err;
+    const double *v;
+    double *w;
+    int32_t nmsg[kLevels];      // message units per level
+    int32_t nunits[kLevels];    // all units per level
+};
+
+template <int MAXJ>
+struct FusedParams {
+    int32_t njobs, kmax, stall;
+    long long timeout_ns, barrier_ns;
+    unsigned int *bar;                 // [0] arrivals, [1] generation (zeroed before launch)
+    unsigned long long *stallctr;      // a counter nothing increments (test hook)
+    int32_t off[kLevels][MAXJ + 1];    // first unit of every job in each level
+    FJob jobs[MAXJ];
+};
+static_assert(sizeof(FusedParams<64>) <= 32764, "kernel parameters are limited to 32,764 bytes");
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch: arrival count and generation.
+// Thread 0 releases the CTA's writes (ordered by the CTA barrier) with its
+// arrival, waits (bounded) for the generation to move, and acquires; the CTA
+// barrier then orders every thread's later loads after it.  The last CTA to
+// arrive resets the count before it publishes the next generation.  A wait
+// that runs out sets every job's error flag and returns false: the CTA stops.
+template <int MAXJ>
+__device__ bool grid_barrier(const FusedParams<MAXJ> &prm)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned *cnt = prm.bar, *gen = prm.bar + 1;
+        const unsigned g = ld_acquire_u32(gen);
+        fence_acq_rel();
+        int ok = 1;
+        if (atomicAdd(cnt, 1u) == gridDim.x - 1) {
+            atomicExch(cnt, 0u);
+            fence_acq_rel();
+            st_release_u32(gen, g + 1);
+        } else {
+            const long long t0 = globaltimer();
+            unsigned ns = 32;
+            while (ld_acquire_u32(gen) == g) {
+                __nanosleep(ns);
+                if (ns < 512) ns <<= 1;
+                if (globaltimer() - t0 > prm.barrier_ns) {
+                    for (int j = 0; j < prm.njobs; j++) atomicCAS(prm.jobs[j].err, 0, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        fence_acq_rel();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Pack and transfer of elements [b, e) in one pass: per element its pack
+// source and destination index first, then the value, g_send written, the
+// value read back from g_send and moved into g_recv.
+__device__ __noinline__ void step_pack_transfer(double *gsend, double *grecv, const double *x,
+                                                const double *lbuf, const uint32_t *src,
+                                                const int32_t *dst, int b, int e, int tid)
+{
+    const uint64_t pol = policy_evict_first();
+    constexpr int U = 8;
+    for (int base = b + tid; base < e; base += NT * U) {
+        uint32_t sv[U];
+        int32_t dv[U];
+        double vv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = base + u * NT;
+            if (k < e) {
+                sv[u] = ld_stream_hint_u32(src + k, pol);
+                dv[u] = ld_stream_hint_s32(dst + k, pol);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = base + u * NT;
+            if (k < e) vv[u] = (sv[u] & kFromLbuf) ? lbuf[sv[u] & ~kFromLbuf] : x[sv[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = base + u * NT;
+            if (k < e) gsend[k] = vv[u];
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = base + u * NT;
+            if (k < e) vv[u] = *(volatile const double *)(gsend + k);
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int k = base + u * NT;
+            if (k < e) grecv[dv[u]] = vv[u];
+        }
+    }
+}
+
+// One unit of level `lvl` of job J (see the level list above).
+template <bool F32, int U>
+__device__ __forceinline__ void fused_unit(const FJob &J, int lvl, int u, const double *x, double *y,
+                                           int tid)
+{
+    const int warp = tid >> 5, lane = tid & 31;
+    const uint64_t pol = policy_evict_first();
+    if (u < J.nmsg[lvl]) {
+        const int b = u * kFusedChunk;
+        switch (lvl) {
+        case 0: {
+            const int nu0 = (J.n0 + kFusedChunk - 1) / kFusedChunk;
+            if (u < nu0) {
+                step_gather<true, 8>(J.bll, x, J.src0, b, min(J.n0, b + kFusedChunk), tid);
+            } else {
+                const int b1 = (u - nu0) * kFusedChunk;
+                step_gather<true, 8>(J.composed ? J.bnl : J.lbuf, x, J.src1, b1,
+                                     min(J.n1, b1 + kFusedChunk), tid);
+            }
+            break;
+        }
+        case 1:
+            step_pack_transfer(J.gsend, J.grecv, x, J.lbuf, J.pack_src, J.xfer_dst, b,
+                               min(J.n_gs, b + kFusedChunk), tid);
+            break;
+        default:
+            step_gather<true, 8>(J.bnl, J.grecv, J.unp_src, b, min(J.n_bnl, b + kFusedChunk), tid);
+            break;
+        }
+        return;
+    }
+    // level 3: chunk groups of the sliced rows, then groups of 8 long rows
+    u -= J.nmsg[lvl];
+    const int ng = (J.F.nch + kSellGroup - 1) / kSellGroup;
+    if (u < ng) {
+        for (int c = u * kSellGroup + warp; c < min(J.F.nch, (u + 1) * kSellGroup); c += WPB)
+            sell_chunk<F32, true, kFull, U>(J.F, c, x, J.bll, J.bnl, y, nullptr, J.scale, lane, pol);
+    } else {
+        const int q = (u - ng) * WPB + warp;
+        if (q < J.F.n_long)
+            row_warp<F32, kFull, true>(J.F.A, x, J.bll, J.bnl, y, nullptr, J.scale, J.F.lrows[q], lane);
+    }
+}
+
+template <bool F32, int U, int MAXJ>
+__global__ void __launch_bounds__(NT, 4) k_fused(const __grid_constant__ FusedParams<MAXJ> prm)
+{
+    const int tid = threadIdx.x;
+    __shared__ int s_skip[MAXJ];
+    for (int k = 0; k < prm.kmax; k++) {
+        for (int lvl = 0; lvl < kLevels; lvl++) {
+            // a job whose flag is set (a wait ran out, in this launch or before)
+            // skips its work; nothing inside a level waits, so the flag is read
+            // once per level (after the barrier that ended the previous one)
+            const int g = (int)gridDim.x;
+            if (tid < prm.njobs) {
+                int skip = *(volatile int *)prm.jobs[tid].err;
+                // test hook: the CTA holding job 0's first unit waits on a
+                // counter nothing increments
+                if (!skip && prm.stall && tid == 0 && k == 0 && lvl == 0 &&
+                    (int)blockIdx.x == prm.off[0][0] % g &&
+                    !wait_ge(prm.stallctr, 1, prm.jobs[0].err, prm.timeout_ns))
+                    skip = 1;
+                s_skip[tid] = skip;
+            }
+            __syncthreads();
+            for (int j = 0; j < prm.njobs; j++) {
+                const FJob &J = prm.jobs[j];
+                if (k >= J.reps || s_skip[j]) continue;
+                const double *x = (k == 0) ? J.v : (((J.reps - k) & 1) == 0 ? J.w : J.xtmp);
+                double *y = (((J.reps - 1 - k) & 1) == 0) ? J.w : J.xtmp;
+                const int base = prm.off[lvl][j];
+                // units u with (base + u) mod grid == this CTA
+                int u = (int)(((long long)blockIdx.x - base) % g);
+                if (u < 0) u += g;
+                for (; u < J.nunits[lvl]; u += g) fused_unit<F32, U>(J, lvl, u, x, y, tid);
+            }
+            if (!grid_barrier(prm)) return;
+        }
+    }
+}
+
 // ------------------------------------------------------------- dispatch
 template <int MAXJ>
 struct FusedKernelTable {
     using Fn = void (*)(const FusedParams<MAXJ>);
-    static Fn get(int vec, bool f32)
+    static Fn get(int unroll, bool f32)
     {
-#define NAP_CASE(V) \
-    case V: return f32 ? k_fused<V, true, MAXJ> : k_fused<V, false, MAXJ>;
-        switch (vec) {
-            NAP_CASE(1)
-            NAP_CASE(2)
-            NAP_CASE(4)
-            NAP_CASE(8)
-            NAP_CASE(16)
-            NAP_CASE(32)
-        }
-#undef NAP_CASE
-        return nullptr;
+        if (unroll == 8) return f32 ? k_fused<true, 8, MAXJ> : k_fused<false, 8, MAXJ>;
+        return f32 ? k_fused<true, 4, MAXJ> : k_fused<false, 4, MAXJ>;
     }
 };
 
@@ -1636,43 +1692,72 @@ static Scale make_scale(double s)
     return sc;
 }
 
-static Job make_job(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
-                    double scale, bool f32)
+// Sliced-row entries per step: 8 where rows average more than 12 stored
+// entries, else 4 (the order of every row's sum does not depend on it).
+static int sell_unroll(const napspmv_plan_t *P) { return P->nnz > 12 * P->n ? 8 : 4; }
+
+// The sliced-row view of one part of the plan (0 whole, 1 local, 2 remote).
+static SellView sell_view(const napspmv_plan_t *P, int part, bool f32)
 {
-    Job J{};
-    J.items = P->items.d_items;
-    J.n_items = P->items.n_items;
-    J.reps = reps;
-    J.scale = make_scale(scale);
-    J.A = Csr3{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
-    J.bll_j = P->lists[L_BLL].d_idx;
-    J.lbuf_j = P->lists[L_LBUF].d_idx;
+    const SellPart &SP = P->sell[part];
+    SellView V{};
+    V.info = SP.d_info;
+    V.perm = SP.d_perm;
+    V.col = SP.d_col;
+    V.val = SP.d_val;
+    V.val32 = SP.d_val32;
+    V.lrows = SP.d_long;
+    V.nch = (int32_t)SP.nch;
+    V.n_long = SP.n_long;
+    V.A = part == 1   ? Csr3{P->d_rowptrL, P->d_colL, P->d_valL, f32 ? P->d_val32L : nullptr}
+          : part == 2 ? Csr3{P->d_rowptrR, P->d_colR, P->d_valR, f32 ? P->d_val32R : nullptr}
+                      : Csr3{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
+    return V;
+}
+
+static int32_t cdiv(int64_t a, int64_t b) { return (int32_t)((a + b - 1) / b); }
+
+static FJob make_job(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
+                     double scale, bool f32)
+{
+    FJob J{};
+    J.F = sell_view(P, 0, f32);
+    J.composed = (P->flags & NAPSPMV_COMPOSED_GATHERS) ? 1 : 0;
+    J.src0 = P->lists[L_BLL].d_idx;
+    J.n0 = (int32_t)P->n_bll;
+    if (J.composed) {
+        J.src1 = P->lists[L_BNL].d_idx;
+        J.n1 = (int32_t)P->n_bnl;
+    } else {
+        J.src1 = P->lists[L_LBUF].d_idx;
+        J.n1 = (int32_t)P->n_lbuf;
+    }
+    J.pack_src = P->d_pack_src;
     J.xfer_dst = P->d_xfer_dst;
     J.unp_src = P->d_unp_src;
-    J.pack_src = P->d_pack_src;
-    J.msg_off = P->d_gs_msg_off;
-    J.msg_dstnode = P->d_gs_msg_dstnode;
-    J.cnt = P->items.d_cnt;
-    J.nn = P->nn;
+    J.n_gs = (int32_t)P->n_gs;
+    J.n_bnl = (int32_t)P->n_bnl;
+    J.reps = reps;
+    J.scale = make_scale(scale);
     J.bll = ws->bll;
     J.lbuf = ws->lbuf;
     J.gsend = ws->gsend;
     J.grecv = ws->grecv;
     J.bnl = ws->bnl;
     J.xtmp = ws->xtmp;
-    J.ctr = ws->ctr;
     J.err = ws->err;
     J.v = v;
     J.w = w;
+    // units of every level: message chunks (levels 0-2), the sliced rows'
+    // chunk groups and long rows (level 3)
+    J.nmsg[0] = cdiv(J.n0, kFusedChunk) + cdiv(J.n1, kFusedChunk);
+    if (!J.composed) {
+        J.nmsg[1] = cdiv(J.n_gs, kFusedChunk);
+        J.nmsg[2] = cdiv(J.n_bnl, kFusedChunk);
+    }
+    for (int l = 0; l < 3; l++) J.nunits[l] = J.nmsg[l];
+    J.nunits[3] = cdiv(J.F.nch, kSellGroup) + cdiv(J.F.n_long, WPB);
     return J;
-}
-
-template <class Fn>
-static int prepare_smem(Fn fn, size_t bytes)
-{
-    if (bytes > 48 * 1024)
-        NAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    return NAPSPMV_OK;
 }
 
 template <int MAXJ>
@@ -1685,60 +1770,47 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
     prm.njobs = count;
     prm.stall = o.debug_stall ? 1 : 0;
     prm.timeout_ns = (long long)o.timeout_ms * 1000000ll;
-    prm.cap = o.tile_nnz;
-    prm.tile_rows = o.tile_rows;
+    prm.barrier_ns = 4 * prm.timeout_ns + 2000000000ll;
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
-    long long total = 0;
-    CtrZero Z;
-    memset(&Z, 0, sizeof(Z));
+    int32_t acc[kLevels] = {};
     for (int i = 0; i < count; i++) {
         napspmv_ws_t *wi = ws && ws[i] ? ws[i] : plans[i]->ws;
         prm.jobs[i] = make_job(plans[i], wi, v[i], w[i], reps[i], scale ? scale[i] : 1.0, f32);
-        prm.jobs[i].tbase = total;
-        total += (long long)prm.jobs[i].n_items * reps[i];
+        prm.kmax = std::max(prm.kmax, reps[i]);
+        for (int l = 0; l < kLevels; l++) {
+            prm.off[l][i] = acc[l];
+            acc[l] += prm.jobs[i].nunits[l];
+        }
         wi->buf_f32 = 0;  // this engine's receive buffers hold FP64 values in both modes
-        Z.p[i] = wi->ctr;
-        Z.n[i] = (int32_t)ctr_count(plans[i]);
     }
-    if (count == 1) {
-        NAP_CUDA(cudaMemsetAsync(Z.p[0], 0, sizeof(unsigned long long) * Z.n[0], s));
-    } else {
-        k_zero_ctrs<<<count, NT, 0, s>>>(Z);
-        NAP_CUDA(cudaGetLastError());
-        count_launch(1);
-    }
-    prm.total = total;
-    bool by_level = MAXJ > 1 && count > 1;
-    for (int i = 1; i < count; i++) by_level = by_level && reps[i] == reps[0];
-    if (by_level) {
-        long long acc = 0;
-        int ns = 0;
-        for (int L = 0; L < 5; L++)
-            for (int i = 0; i < count; i++) {
-                const int32_t *lv = plans[i]->items.lvl;
-                if (lv[L + 1] > lv[L]) {
-                    prm.seg[ns].t0 = acc;
-                    prm.seg[ns].job = i;
-                    prm.seg[ns].item0 = lv[L];
-                    ns++;
-                    acc += lv[L + 1] - lv[L];
-                }
-            }
-        prm.nseg = ns;
-        prm.period = acc;
-        prm.total = acc * reps[0];  // the same count as job after job
-    }
-    prm.ticket = prm.jobs[0].ctr;
-    auto fn = FusedKernelTable<MAXJ>::get(o.vec, f32);
-    const size_t sm = smem_bytes(o.tile_nnz, o.tile_rows);
-    if (int rc = prepare_smem(fn, sm)) return rc;
+    for (int l = 0; l < kLevels; l++) prm.off[l][count] = acc[l];
+    // barrier words and the test hook's counter: the first job's counters
+    napspmv_ws_t *w0 = ws && ws[0] ? ws[0] : plans[0]->ws;
+    prm.bar = reinterpret_cast<unsigned int *>(w0->ctr);
+    prm.stallctr = w0->ctr + 1;
+    NAP_CUDA(cudaMemsetAsync(w0->ctr, 0, 2 * sizeof(unsigned long long), s));
+    auto fn = FusedKernelTable<MAXJ>::get(sell_unroll(plans[0]), f32);
+    NAP_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
     int occ = 0;
-    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, sm));
-    int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
-    long long grid = (long long)plans[0]->num_sms * per_sm;
-    grid = std::max(1ll, std::min(grid, total));
-    fn<<<(int)grid, NT, sm, s>>>(prm);
-    NAP_CUDA(cudaGetLastError());
+    NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, 0));
+    if (occ < 1) {
+        set_error(NAPSPMV_ERR_CUDA, "fused engine: no CTA fits on an SM");
+        return NAPSPMV_ERR_CUDA;
+    }
+    const int per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, occ) : occ;
+    // every CTA resident at once (cooperative launch): the level barriers
+    // never wait on a CTA that has not started
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(plans[0]->num_sms * per_sm));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    NAP_CUDA(cudaLaunchKernelEx(&cfg, fn, prm));
     count_launch(1);
     return NAPSPMV_OK;
 }
@@ -1784,9 +1856,25 @@ static HaloKernel pick_halo(int vec)
     }
 }
 
+using SellKernel = void (*)(SellView, const void *, const void *, const void *, double *, float *,
+                            Scale, int *);
+template <bool F32, int U>
+static SellKernel pick_sell_u(int mode)
+{
+    return mode == kLocal ? k_spmv_s<F32, kLocal, U>
+                          : mode == kRemote ? k_spmv_s<F32, kRemote, U> : k_spmv_s<F32, kFull, U>;
+}
+template <bool F32>
+static SellKernel pick_sell(int mode, int unroll)
+{
+    return unroll == 8 ? pick_sell_u<F32, 8>(mode) : pick_sell_u<F32, 4>(mode);
+}
+
 struct SpmvLaunch {
     SpmvKernel fn = nullptr;
     HaloKernel hfn = nullptr;  // set: the remote pass with staged receive buffers
+    SellKernel sfn = nullptr;  // set: the sliced-row pass
+    SellView S{};
     Csr3 A{};
     const Item *tiles = nullptr;
     const int32_t *bll_rank = nullptr, *bnl_rank = nullptr;
@@ -1803,7 +1891,8 @@ struct SpmvLaunch {
 // CTA per SM); the stencils (2-6 remote entries per row) lose 5-7%.
 static size_t halo_smem(const napspmv_plan_t *P, const napspmv_opts &o)
 {
-    if (o.halo != NAPSPMV_HALO_ON || (P->flags & NAPSPMV_PARTITION_STRIDED) ||
+    if (o.halo != NAPSPMV_HALO_ON || o.pipeline == NAPSPMV_PIPELINE_SELL ||
+        (P->flags & NAPSPMV_PARTITION_STRIDED) ||
         P->h_bll_rank.size() != (size_t)P->np + 1 || P->items.n_tilesRH == 0 ||
         P->nnzR < 8 * P->n)
         return 0;
@@ -1828,6 +1917,26 @@ static size_t halo_smem(const napspmv_plan_t *P, const napspmv_opts &o)
 static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode, SpmvLaunch &L)
 {
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
+    if (o.pipeline == NAPSPMV_PIPELINE_SELL) {
+        const int part = mode == kLocal ? 1 : mode == kRemote ? 2 : 0;
+        const SellPart &SP = P->sell[part];
+        L.sfn = f32 ? pick_sell<true>(mode, sell_unroll(P)) : pick_sell<false>(mode, sell_unroll(P));
+        L.S = sell_view(P, part, f32);
+        L.sm = 0;
+        const void *kf = (const void *)L.sfn;
+        // no shared memory: the whole unified L1 / shared storage is L1
+        NAP_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        int occ = 0;
+        NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf, NT, 0));
+        if (o.ctas_per_sm > 0) occ = std::min(occ, o.ctas_per_sm);
+        const int64_t ctas = std::max<int64_t>((SP.nch + kSellGroup - 1) / kSellGroup,
+                                               (SP.n_long + WPB - 1) / WPB);
+        L.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)P->num_sms * std::max(occ, 1)));
+        if (mode == kLocal)  // leave one CTA slot per SM for the message steps
+            L.grid = (int)std::max<int64_t>(
+                1, std::min<int64_t>(ctas, (int64_t)P->num_sms * std::max(occ - 1, 1)));
+        return NAPSPMV_OK;
+    }
     const bool warp = o.pipeline == NAPSPMV_PIPELINE_WARP;
     const ItemSet &S = P->items;
     const int list = (warp ? 3 : 0) + (mode == kLocal ? 1 : mode == kRemote ? 2 : 0);
@@ -1920,7 +2029,10 @@ static void launch_pdl(bool pdl, void (*kern)(KArgs...), int grid, size_t smem, 
 static void spmv_run(const SpmvLaunch &L, const void *x, const napspmv_ws_t *ws, double *y,
                      float *y32, double scale, int stages, cudaStream_t s, bool pdl)
 {
-    if (L.hfn)
+    if (L.sfn)
+        launch_pdl(pdl, L.sfn, L.grid, 0, s, L.S, x, (const void *)ws->bll, (const void *)ws->bnl,
+                   y, y32, make_scale(scale), ws->err);
+    else if (L.hfn)
         launch_pdl(pdl, L.hfn, L.grid, L.sm, s, L.A, (const void *)ws->bll, (const void *)ws->bnl,
                    y, y32, make_scale(scale), L.tiles, L.n, L.cap, L.rows, stages, L.bll_rank,
                    L.bnl_rank, ws->err);
@@ -2115,7 +2227,7 @@ static int launch_phased(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, d
     return NAPSPMV_OK;
 }
 
-static int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
+int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
 {
     if (!valid_vec(o.vec)) {
         set_error(NAPSPMV_ERR_ARG, "vec must be 1, 2, 4, 8, 16 or 32");
@@ -2134,14 +2246,9 @@ static int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
         set_error(NAPSPMV_ERR_ARG, "unknown engine");
         return NAPSPMV_ERR_ARG;
     }
-    if (o.engine == NAPSPMV_ENGINE_FUSED && (P->flags & NAPSPMV_PARTITION_STRIDED)) {
-        set_error(NAPSPMV_ERR_UNSUPPORTED, "the fused engine needs contiguous node rows; a "
-                                           "strided plan runs on the phased or overlapped engine");
-        return NAPSPMV_ERR_UNSUPPORTED;
-    }
-    if (o.engine == NAPSPMV_ENGINE_FUSED && (P->flags & NAPSPMV_COMPOSED_GATHERS)) {
-        set_error(NAPSPMV_ERR_UNSUPPORTED, "composed gathers run on the phased or overlapped "
-                                           "engine only");
+    if (o.engine == NAPSPMV_ENGINE_FUSED && P->sell[0].slots < 0) {
+        set_error(NAPSPMV_ERR_UNSUPPORTED, "the fused engine sums rows from the sliced-row copy, "
+                                           "which this plan could not keep (over 2^31 slots)");
         return NAPSPMV_ERR_UNSUPPORTED;
     }
     if (o.timeout_ms < 1) {
@@ -2152,9 +2259,16 @@ static int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
         set_error(NAPSPMV_ERR_ARG, "halo must be NAPSPMV_HALO_ON or _OFF");
         return NAPSPMV_ERR_ARG;
     }
-    if (o.pipeline != NAPSPMV_PIPELINE_CTA && o.pipeline != NAPSPMV_PIPELINE_WARP) {
-        set_error(NAPSPMV_ERR_ARG, "pipeline must be NAPSPMV_PIPELINE_CTA or _WARP");
+    if (o.pipeline != NAPSPMV_PIPELINE_CTA && o.pipeline != NAPSPMV_PIPELINE_WARP &&
+        o.pipeline != NAPSPMV_PIPELINE_SELL) {
+        set_error(NAPSPMV_ERR_ARG, "pipeline must be NAPSPMV_PIPELINE_CTA, _WARP or _SELL");
         return NAPSPMV_ERR_ARG;
+    }
+    if (o.pipeline == NAPSPMV_PIPELINE_SELL &&
+        (P->sell[0].slots < 0 || P->sell[1].slots < 0 || P->sell[2].slots < 0)) {
+        set_error(NAPSPMV_ERR_UNSUPPORTED, "the sliced-row copy of this plan would exceed 2^31 "
+                                           "slots; use the CTA or warp pipeline");
+        return NAPSPMV_ERR_UNSUPPORTED;
     }
     if (o.stages < 2 || o.stages > kMaxStages ||
         smem_bytes(o.tile_nnz, o.tile_rows, o.stages) > 220 * 1024) {
@@ -2163,6 +2277,16 @@ static int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
         return NAPSPMV_ERR_ARG;
     }
     return NAPSPMV_OK;
+}
+
+// Launch-relevant fields of two resolved option sets agree: entries with equal
+// keys can share one fused launch (one kernel, one lane count, one tile shape).
+static bool same_launch(const napspmv_opts &a, const napspmv_opts &b)
+{
+    return a.precision == b.precision && a.vec == b.vec && a.chunk == b.chunk &&
+           a.tile_rows == b.tile_rows && a.tile_nnz == b.tile_nnz &&
+           a.ctas_per_sm == b.ctas_per_sm && a.timeout_ms == b.timeout_ms &&
+           a.debug_stall == b.debug_stall;
 }
 
 int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const *ws,
@@ -2178,7 +2302,9 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
         set_error(NAPSPMV_ERR_ARG, "NULL plan");
         return NAPSPMV_ERR_ARG;
     }
-    napspmv_opts o = resolve_opts(P0, opts);
+    // every entry resolves the unset fields against its own plan's defaults,
+    // so that it runs with the work items its plan already holds
+    napspmv_opts oi[64];
     int cur = 0;
     NAP_CUDA(cudaGetDevice(&cur));
     if (cur != P0->device) NAP_CUDA(cudaSetDevice(P0->device));
@@ -2195,15 +2321,9 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
             rc = NAPSPMV_ERR_ARG;
             break;
         }
-        if (count > 1 && (P->flags & (NAPSPMV_PARTITION_STRIDED | NAPSPMV_COMPOSED_GATHERS))) {
-            set_error(NAPSPMV_ERR_UNSUPPORTED,
-                      "batched applies run the fused engine, which needs contiguous node rows "
-                      "and literal exchanges (no strided or composed-gather plans)");
-            rc = NAPSPMV_ERR_UNSUPPORTED;
-            break;
-        }
-        if ((rc = check_opts(P, o))) break;
-        if ((rc = build_items(P, o.chunk, o.tile_rows, o.tile_nnz))) break;
+        oi[i] = resolve_opts(P, opts);
+        if ((rc = check_opts(P, oi[i]))) break;
+        if ((rc = build_items(P, oi[i].chunk, oi[i].tile_rows, oi[i].tile_nnz))) break;
         for (int q = 0; q < i; q++) {
             napspmv_ws_t *a = ws && ws[i] ? ws[i] : P->ws;
             napspmv_ws_t *b = ws && ws[q] ? ws[q] : plans[q]->ws;
@@ -2218,14 +2338,41 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
             rc = NAPSPMV_ERR_ARG;
         }
     }
-    if (!rc) {
-        if (count == 1 && (o.engine == NAPSPMV_ENGINE_PHASED || o.engine == NAPSPMV_ENGINE_OVERLAP))
+    if (!rc && count == 1) {
+        const napspmv_opts &o = oi[0];
+        if (o.engine == NAPSPMV_ENGINE_PHASED || o.engine == NAPSPMV_ENGINE_OVERLAP)
             rc = launch_phased(P0, ws && ws[0] ? ws[0] : P0->ws, v[0], w[0], reps[0],
                                scale ? scale[0] : 1.0, o, s);
-        else if (count == 1)
-            rc = launch_fused<1>(count, plans, ws, v, w, reps, scale, o, s);
         else
-            rc = launch_fused<64>(count, plans, ws, v, w, reps, scale, o, s);
+            rc = launch_fused<1>(1, plans, ws, v, w, reps, scale, o, s);
+    } else if (!rc) {
+        // one fused launch per distinct launch option set, in order of first
+        // appearance; an entry's bits are those of its plan applied alone on the
+        // fused engine with its resolved options, whatever else is in the batch
+        bool done[64] = {};
+        for (int i = 0; i < count && !rc; i++) {
+            if (done[i]) continue;
+            napspmv_plan_t *gp[64];
+            napspmv_ws_t *gw[64];
+            const double *gv[64];
+            double *gx[64];
+            int32_t gr[64];
+            double gs[64];
+            int m = 0;
+            for (int j = i; j < count; j++) {
+                if (done[j] || !same_launch(oi[i], oi[j])) continue;
+                done[j] = true;
+                gp[m] = plans[j];
+                gw[m] = ws && ws[j] ? ws[j] : plans[j]->ws;
+                gv[m] = v[j];
+                gx[m] = w[j];
+                gr[m] = reps[j];
+                gs[m] = scale ? scale[j] : 1.0;
+                m++;
+            }
+            rc = m == 1 ? launch_fused<1>(1, gp, gw, gv, gx, gr, gs, oi[i], s)
+                        : launch_fused<64>(m, gp, gw, gv, gx, gr, gs, oi[i], s);
+        }
     }
     if (cur != P0->device) cudaSetDevice(cur);
     return rc;
@@ -2262,15 +2409,12 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
         set_error(NAPSPMV_ERR_ARG, "NULL plan or vector, reps < 1, or w == v");
         return NAPSPMV_ERR_ARG;
     }
-    if (P->flags & (NAPSPMV_PARTITION_STRIDED | NAPSPMV_COMPOSED_GATHERS)) {
-        set_error(NAPSPMV_ERR_UNSUPPORTED, "napspmv_apply_noalloc runs the fused engine, which "
-                                           "needs contiguous node rows and literal exchanges");
-        return NAPSPMV_ERR_UNSUPPORTED;
-    }
     // doubles of scratch: counters (as 8-byte words), b_{l->l}, b_{l->nl},
-    // g_send, g_recv, b_{nl->l}, the chain vector
+    // g_send, g_recv, b_{nl->l}, and the chain vector when reps > 1 (a single
+    // apply writes w directly)
     const int64_t words = (int64_t)ctr_count(P);
-    const int64_t need = words + P->n_bll + P->n_lbuf + 2 * P->n_gs + P->n_bnl + P->n;
+    const int64_t need = words + P->n_bll + P->n_lbuf + 2 * P->n_gs + P->n_bnl +
+                         (reps > 1 ? P->n : 0);
     if (need > kNoallocDoubles) {
         set_error(NAPSPMV_ERR_UNSUPPORTED,
                   "napspmv_apply_noalloc: this plan needs " + std::to_string(need) +
@@ -2288,7 +2432,9 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
     double *base = nullptr;
     {
         // first call on a device: look up the array's device address (with
-        // that device current); later calls reuse it
+        // that device current); later calls reuse it.  The cached address
+        // belongs to the device's current context: it does not survive
+        // cudaDeviceReset.
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
         if (!g_noalloc_ptr[P->device]) {
             void *p = nullptr;
@@ -2317,7 +2463,7 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
     q += P->n_gs;
     view.bnl = q;
     q += P->n_bnl;
-    view.xtmp = q;
+    view.xtmp = reps > 1 ? q : nullptr;
     view.err = P->ws->err;
     // the plan's current work items and matching options: nothing is rebuilt
     napspmv_opts o = P->defaults;
@@ -2327,6 +2473,10 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
     o.tile_rows = P->items.tile_rows;
     o.tile_nnz = P->items.tile_nnz;
     o.debug_stall = 0;
+    if (int rc2 = check_opts(P, o)) {
+        if (cur != P->device) cudaSetDevice(cur);
+        return rc2;
+    }
     napspmv_ws_t *wsl[1] = {&view};
     napspmv_plan_t *pl[1] = {P};
     const double *vl[1] = {v};

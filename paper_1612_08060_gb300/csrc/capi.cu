@@ -209,15 +209,16 @@ int napspmv_set_default_opts(napspmv_plan_t *P, const napspmv_opts *opts)
 {
     if (!P || !opts) return arg_error("NULL plan or opts");
     napspmv_opts o = resolve_opts(P, opts);
-    if (!(o.vec == 1 || o.vec == 2 || o.vec == 4 || o.vec == 8 || o.vec == 16 || o.vec == 32))
-        return arg_error("vec must be 1, 2, 4, 8, 16 or 32");
+    o.debug_stall = 0;
+    // every field is checked before it becomes a default (a bad timeout or
+    // stage count would otherwise reach the kernels of later applies)
+    if (int rc = check_opts(P, o)) return rc;
     int cur = 0;
     NAP_CUDA(cudaGetDevice(&cur));
     if (cur != P->device) NAP_CUDA(cudaSetDevice(P->device));
     int rc = build_items(P, o.chunk, o.tile_rows, o.tile_nnz);
     if (cur != P->device) cudaSetDevice(cur);
     if (rc) return rc;
-    o.debug_stall = 0;
     P->defaults = o;
     return NAPSPMV_OK;
 }

@@ -94,6 +94,30 @@ struct HostList {
 
 enum ListKind { L_STD = 0, L_NODE, L_INTER, L_J0, L_J1, L_J2, L_BLL, L_BNL, L_LBUF, L_COUNT };
 
+// ------------------------------------------------------- sliced rows (SELL)
+// One matrix part (whole, local or remote) in sliced-row form: the rows of
+// each process (of each 1024-row block for a strided plan) are sorted by
+// stored-entry count, longest first (ties by row), and cut into chunks of up
+// to 32 rows whose counts lie within a factor of two of the chunk's first.
+// Chunk c stores entry i of its lane l at slot info[c].x + i * lanes + l
+// (column-major, so a warp reads consecutive slots); a lane's row shorter
+// than the chunk's width is padded with kSellPad columns.  Each row keeps its
+// stored entry order, so one lane summing it gives the same bits as the
+// one-lane-per-row CSR kernels.  Rows longer than kSellLong entries are listed
+// apart and summed by a whole warp from the CSR part.
+constexpr uint32_t kSellPad = 0xffffffffu;
+constexpr int32_t kSellLong = 256;
+struct SellPart {
+    int64_t nch = 0, slots = 0;
+    int32_t n_long = 0;
+    int2 *d_info = nullptr;     // per chunk: first slot, (width << 6) | lanes
+    int32_t *d_perm = nullptr;  // 32 per chunk: the row of each lane (-1: none)
+    uint32_t *d_col = nullptr;  // block-coded columns, kSellPad in the padding
+    double *d_val = nullptr;
+    float *d_val32 = nullptr;
+    int32_t *d_long = nullptr;  // rows of more than kSellLong entries
+};
+
 }  // namespace nap
 
 struct napspmv_ws_s {
@@ -159,6 +183,10 @@ struct napspmv_plan_s {
     int32_t *d_gs_msg_off = nullptr;       // device copies
     int32_t *d_gs_msg_dstnode = nullptr;
 
+    // sliced-row copies of the whole matrix, its local part and its remote
+    // part (index 0, 1, 2), for NAPSPMV_PIPELINE_SELL; built with the plan
+    nap::SellPart sell[3];
+
     nap::ItemSet items;
     // instantiated CUDA graphs of chained phased applies, newest last
     struct GraphEntry {
@@ -180,6 +208,9 @@ int ws_alloc(napspmv_plan_t *P, napspmv_ws_t *ws);
 void ws_free(napspmv_ws_t *ws);
 void plan_free(napspmv_plan_t *P);
 napspmv_opts resolve_opts(const napspmv_plan_t *P, const napspmv_opts *o);
+// ERR_ARG / ERR_STATE / ERR_UNSUPPORTED (with the message set) for resolved
+// options the plan cannot run, else NAPSPMV_OK
+int check_opts(const napspmv_plan_t *P, const napspmv_opts &o);
 int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const *ws,
                 const double *const *v, double *const *w, const int32_t *reps,
                 const double *scale, const napspmv_opts *opts, cudaStream_t s);

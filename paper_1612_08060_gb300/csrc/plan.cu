@@ -238,9 +238,10 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, 
 // destinations in g_recv, the message of every element and the J0 keys.
 __global__ void k_fill_gsend(int64_t n_gs, const int64_t *gs_off, int64_t n_msg,
                              const int32_t *msg_pair, const int32_t *msg_src,
-                             const int64_t *pair_gr_off, const int32_t *node_ptr,
-                             const int32_t *node_idx, Part part, int rb, int jb, int32_t *gs_j,
-                             int32_t *xfer_dst, int32_t *msg_of, uint64_t *j0key)
+                             const int64_t *msg_gr, const int64_t *msg_lo,
+                             const int32_t *node_ptr, const int32_t *node_idx, Part part, int rb,
+                             int jb, int32_t *gs_j, int32_t *xfer_dst, int32_t *msg_of,
+                             uint64_t *j0key)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_gs;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -254,9 +255,9 @@ __global__ void k_fill_gsend(int64_t n_gs, const int64_t *gs_off, int64_t n_msg,
         }
         int32_t k = msg_pair[lo];
         int64_t off = e - gs_off[lo];
-        int32_t j = node_idx[node_ptr[k] + off];
+        int32_t j = node_idx[node_ptr[k] + msg_lo[lo] + off];
         gs_j[e] = j;
-        xfer_dst[e] = (int32_t)(pair_gr_off[k] + off);
+        xfer_dst[e] = (int32_t)(msg_gr[lo] + off);
         msg_of[e] = (int32_t)lo;
         int64_t s = msg_src[lo], p = part.owner(j);
         j0key[e] = (p != s) ? (((uint64_t)p << (rb + jb)) | ((uint64_t)s << jb) | (uint64_t)j)
@@ -286,7 +287,8 @@ __global__ void k_pack_src(int64_t n_gs, const int32_t *gs_j, const int32_t *msg
 // the J1 key (q, t, j) when q != t, and the g_recv position to unpack from.
 __global__ void k_unpack_src(int64_t n_bnl, const uint64_t *bnl_keys, int jb, Part part,
                              int32_t ppn, int nb, int64_t n_pairs, const uint64_t *pair_key,
-                             const int32_t *recv_proc, const int64_t *pair_gr_off,
+                             const int64_t *pair_piece, const int64_t *piece_lo,
+                             const int32_t *piece_dst, const int64_t *piece_gr,
                              const int32_t *node_ptr, const int32_t *node_idx, int rb,
                              uint64_t *j1key, int32_t *unp_src, int *bad)
 {
@@ -311,13 +313,29 @@ __global__ void k_unpack_src(int64_t n_bnl, const uint64_t *bnl_keys, int jb, Pa
             j1key[e] = SENT;
             continue;
         }
-        int64_t q = (int64_t)m * ppn + recv_proc[lo];
-        j1key[e] = ((int64_t)t != q) ? (((uint64_t)q << (rb + jb)) | (t << jb) | (uint64_t)j)
-                                     : SENT;
         int64_t b = node_ptr[lo], len = node_ptr[lo + 1] - b;
         int64_t pos = lower_bound_i32(node_idx + b, len, j);
         if (pos >= len || node_idx[b + pos] != j) atomicOr(bad, 16);
-        unp_src[e] = (int32_t)(pair_gr_off[lo] + pos);
+        // the piece of the pair holding position pos: the last one starting at
+        // or before it
+        int64_t a = pair_piece[lo], z = pair_piece[lo + 1] - 1;
+        if (z < a) {
+            atomicOr(bad, 16);
+            unp_src[e] = 0;
+            j1key[e] = SENT;
+            continue;
+        }
+        while (a < z) {
+            int64_t mid = (a + z + 1) >> 1;
+            if (piece_lo[mid] <= pos)
+                a = mid;
+            else
+                z = mid - 1;
+        }
+        int64_t q = piece_dst[a];
+        j1key[e] = ((int64_t)t != q) ? (((uint64_t)q << (rb + jb)) | (t << jb) | (uint64_t)j)
+                                     : SENT;
+        unp_src[e] = (int32_t)(piece_gr[a] + pos - piece_lo[a]);
     }
 }
 
@@ -463,6 +481,30 @@ struct Cub {
         CK(cudaMemcpy(len.data(), c.p, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
     }
 };
+
+// Sliced rows: one warp per chunk copies each lane's row into the chunk's
+// column-major slots (slot first + i * lanes + lane holds entry i of the
+// lane's row) and pads the slots past the row's end.
+__global__ void k_sell_fill(const int32_t *rp, const uint32_t *col, const double *val,
+                            const float *val32, const int2 *info, const int32_t *perm,
+                            int64_t nch, uint32_t *scol, double *sval, float *sval32)
+{
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= nch) return;
+    const int2 inf = info[c];
+    const int width = inf.y >> 6, nl = inf.y & 63;
+    if (lane >= nl) return;
+    const int row = perm[32 * c + lane];
+    const int k0 = rp[row], len = rp[row + 1] - k0;
+    for (int i = 0; i < width; i++) {
+        const int64_t q = (int64_t)inf.x + (int64_t)i * nl + lane;
+        const bool in = i < len;
+        scol[q] = in ? col[k0 + i] : kSellPad;
+        sval[q] = in ? val[k0 + i] : 0.0;
+        if (sval32) sval32[q] = in ? val32[k0 + i] : 0.0f;
+    }
+}
 
 // A sorted, unique key array (prefix << jb | j) becomes a message list whose
 // prefix is (src << fb | dst); with fb < 0 the prefix is one process id used
@@ -627,6 +669,78 @@ void host_stats(napspmv_plan_t *P)
     S.bytes_msg = 20.0 * (double)(P->n_bll + P->n_lbuf + P->n_gs + P->n_bnl) + 20.0 * (double)P->n_gs;
 }
 
+// Sliced-row copy of one matrix part (which: 0 whole, 1 local, 2 remote) from
+// its CSR (host row pointer hrp, device arrays).  Windows: the rows of each
+// process (contiguous partition) or of each 1024-row block (strided).  Within
+// a window, rows of at most kSellLong entries are sorted by count, longest
+// first (ties by row), and cut into chunks of up to 32 whose counts are at
+// least half the first one's; longer rows are listed apart.  A part whose
+// padded slots would not fit 31-bit offsets is left without a sliced copy.
+void build_sell(napspmv_plan_t *P, int which, const std::vector<int32_t> &hrp,
+                const int32_t *d_rp, const uint32_t *d_col, const double *d_val,
+                const float *d_val32, const Part &part)
+{
+    SellPart &S = P->sell[which];
+    const int64_t n = P->n;
+    std::vector<int2> info;
+    std::vector<int32_t> perm, lrows, ord;
+    int64_t slots = 0;
+    auto len = [&](int32_t r) { return hrp[r + 1] - hrp[r]; };
+    auto window = [&](int64_t r0, int64_t r1) {
+        ord.clear();
+        for (int64_t r = r0; r < r1; r++) {
+            if (len((int32_t)r) > kSellLong) lrows.push_back((int32_t)r);
+            else ord.push_back((int32_t)r);
+        }
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int32_t a, int32_t b) { return len(a) > len(b); });
+        size_t j = 0;
+        while (j < ord.size()) {
+            const int32_t w = len(ord[j]);
+            size_t e = j + 1;
+            while (e < ord.size() && e - j < 32 && 2 * len(ord[e]) >= w) e++;
+            const int nl = (int)(e - j);
+            info.push_back(make_int2((int)std::min<int64_t>(slots, INT32_MAX), (w << 6) | nl));
+            for (int l = 0; l < 32; l++) perm.push_back(l < nl ? ord[j + l] : -1);
+            // every chunk starts on a 4-slot (16-byte) boundary: its column
+            // blocks are copied into shared memory with bulk copies
+            slots += ((int64_t)w * nl + 3) & ~3ll;
+            j = e;
+        }
+    };
+    if (part.strided) {
+        for (int64_t r0 = 0; r0 < n; r0 += 1024) window(r0, std::min<int64_t>(n, r0 + 1024));
+    } else {
+        for (int64_t r = 0; r < part.np; r++) window(part.start(r), part.start(r + 1));
+    }
+    if (slots > (int64_t)INT32_MAX - 1024) {
+        S.slots = -1;  // no sliced copy: NAPSPMV_PIPELINE_SELL is refused for this plan
+        return;
+    }
+    S.nch = (int64_t)info.size();
+    S.slots = slots;
+    S.n_long = (int32_t)lrows.size();
+    S.d_info = upload(info);
+    S.d_perm = upload(perm);
+    S.d_long = upload(lrows);
+    // padded past the last slot: a block's bulk copy is widened to 16 bytes
+    auto al = [&](size_t sz) {
+        void *q = nullptr;
+        CK(cudaMalloc(&q, sz * (size_t)std::max<int64_t>(slots, 1) + 256));
+        CK(cudaMemset(q, 0, sz * (size_t)std::max<int64_t>(slots, 1) + 256));
+        return q;
+    };
+    S.d_col = (uint32_t *)al(4);
+    S.d_val = (double *)al(8);
+    if (d_val32) S.d_val32 = (float *)al(4);
+    if (S.nch) {
+        k_sell_fill<<<blocks_for(32 * S.nch), 256>>>(d_rp, d_col, d_val, d_val32, S.d_info,
+                                                     S.d_perm, S.nch, S.d_col, S.d_val,
+                                                     S.d_val32);
+        CK(cudaGetLastError());
+    }
+}
+
 void build(napspmv_plan_t *P, const napspmv_csr *A)
 {
     const int64_t n = A->n, nnz = A->nnz;
@@ -738,6 +852,8 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
     const int64_t M = ND.m;
     P->send_proc.assign(M, 0);
     P->recv_proc.assign(M, 0);
+    // processes per pair on each side: 1, or a group when the node is split
+    std::vector<int32_t> send_cnt(M, 1), recv_cnt(M, 1);
     {
         auto procs = [&](int64_t node) { return (int64_t)std::min<int64_t>(ppn, np - node * ppn); };
         std::vector<std::vector<int64_t>> out_of(nn), in_of(nn);
@@ -789,76 +905,143 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
                 if (len(a) != len(b)) return len(a) > len(b);
                 return ND.dst[a] < ND.dst[b];
             });
-            for (size_t k = 0; k < o.size(); k++) P->send_proc[o[k]] = (int32_t)(k % procs(x));
+            const int64_t px = procs(x);
+            const bool split = (P->flags & NAPSPMV_MAP_SPLIT) != 0;
+            // node splitting (the text after Eq. U): fewer partners than
+            // processes -> partner k gets px / K (+1 for the first px mod K)
+            // consecutive processes, counted up from process 0 when sending
+            if (split && (int64_t)o.size() < px) {
+                const int64_t K = (int64_t)o.size();
+                int64_t first = 0;
+                for (int64_t k = 0; k < K; k++) {
+                    const int64_t size = px / K + (k < px % K ? 1 : 0);
+                    P->send_proc[o[k]] = (int32_t)first;
+                    send_cnt[o[k]] = (int32_t)size;
+                    first += size;
+                }
+            } else {
+                for (size_t k = 0; k < o.size(); k++) P->send_proc[o[k]] = (int32_t)(k % px);
+            }
             auto &i = in_of[x];
             bool text = (P->flags & NAPSPMV_MAP_TEXT) != 0;
             std::stable_sort(i.begin(), i.end(), [&](int64_t a, int64_t b) {
                 if (len(a) != len(b)) return text ? len(a) > len(b) : len(a) < len(b);
                 return ND.src[a] < ND.src[b];
             });
-            for (size_t k = 0; k < i.size(); k++)
-                P->recv_proc[i[k]] = (int32_t)(procs(x) - 1 - (int64_t)(k % procs(x)));
+            // receiving: groups counted down from the last process
+            if (split && (int64_t)i.size() < px) {
+                const int64_t K = (int64_t)i.size();
+                int64_t top = px;
+                for (int64_t k = 0; k < K; k++) {
+                    const int64_t size = px / K + (k < px % K ? 1 : 0);
+                    P->recv_proc[i[k]] = (int32_t)(top - size);
+                    recv_cnt[i[k]] = (int32_t)size;
+                    top -= size;
+                }
+            } else {
+                for (size_t k = 0; k < i.size(); k++)
+                    P->recv_proc[i[k]] = (int32_t)(px - 1 - (int64_t)(k % px));
+            }
         }
     }
 
     // ---- G, I: one message per node pair, in (src, dst) order for g_send and
-    // (dst, src) order for g_recv
-    std::vector<int32_t> psrc(M), pdst(M);
+    // (dst, src) order for g_recv.  With node splitting a pair carries
+    // c = max(send group, receive group) messages: piece i of E(n,m) (positions
+    // floor(i e / c) .. floor((i + 1) e / c) - 1) from the i-th process of the
+    // sending group to the i-th of the receiving group, cyclically; empty
+    // pieces are no message.
+    struct Msg {
+        int32_t pair, src, dst;
+        int64_t lo, hi;  // positions in E(n,m)
+    };
+    std::vector<Msg> msgs;
+    msgs.reserve(M);
+    std::vector<int64_t> pair_piece(M + 1, 0);  // first message (by pair) of each pair
     for (int64_t k = 0; k < M; k++) {
-        psrc[k] = ND.src[k] * ppn + P->send_proc[k];
-        pdst[k] = ND.dst[k] * ppn + P->recv_proc[k];
+        const int64_t ns = send_cnt[k], nr = recv_cnt[k], c = std::max(ns, nr);
+        const int64_t e = ND.ptr[k + 1] - ND.ptr[k];
+        for (int64_t i = 0; i < c; i++) {
+            const int64_t lo = i * e / c, hi = (i + 1) * e / c;
+            if (hi == lo) continue;
+            Msg mg;
+            mg.pair = (int32_t)k;
+            mg.src = (int32_t)(ND.src[k] * ppn + P->send_proc[k] + i % ns);
+            mg.dst = (int32_t)(ND.dst[k] * ppn + P->recv_proc[k] + i % nr);
+            mg.lo = lo;
+            mg.hi = hi;
+            msgs.push_back(mg);
+        }
+        pair_piece[k + 1] = (int64_t)msgs.size();
     }
-    std::vector<int32_t> sorder(M), rorder(M);
+    const int64_t NM = (int64_t)msgs.size();
+    std::vector<int32_t> sorder(NM), rorder(NM);
     std::iota(sorder.begin(), sorder.end(), 0);
     std::iota(rorder.begin(), rorder.end(), 0);
     std::sort(sorder.begin(), sorder.end(), [&](int32_t a, int32_t b) {
-        return psrc[a] != psrc[b] ? psrc[a] < psrc[b] : pdst[a] < pdst[b];
+        return msgs[a].src != msgs[b].src ? msgs[a].src < msgs[b].src : msgs[a].dst < msgs[b].dst;
     });
     std::sort(rorder.begin(), rorder.end(), [&](int32_t a, int32_t b) {
-        return pdst[a] != pdst[b] ? pdst[a] < pdst[b] : psrc[a] < psrc[b];
+        return msgs[a].dst != msgs[b].dst ? msgs[a].dst < msgs[b].dst : msgs[a].src < msgs[b].src;
     });
-    std::vector<int64_t> gs_off(M + 1, 0), pair_gr_off(M, 0);
-    std::vector<int32_t> msg_src(M), msg_dstnode(M);
-    for (int64_t i = 0; i < M; i++) {
-        int32_t k = sorder[i];
-        gs_off[i + 1] = gs_off[i] + (ND.ptr[k + 1] - ND.ptr[k]);
-        msg_src[i] = psrc[k];
-        msg_dstnode[i] = ND.dst[k];
-    }
+    // g_recv offset of every message (indexed by message in pair order)
+    std::vector<int64_t> gr_off(NM, 0);
     {
         int64_t o = 0;
-        for (int64_t i = 0; i < M; i++) {
-            int32_t k = rorder[i];
-            pair_gr_off[k] = o;
-            o += ND.ptr[k + 1] - ND.ptr[k];
+        for (int64_t i = 0; i < NM; i++) {
+            gr_off[rorder[i]] = o;
+            o += msgs[rorder[i]].hi - msgs[rorder[i]].lo;
         }
     }
-    P->n_gs = gs_off[M];
+    // g_send in (src, dst) order: offsets, and per message (in that order) its
+    // pair, first position in E(n,m), sender and g_recv offset
+    std::vector<int64_t> gs_off(NM + 1, 0), msg_gr(NM), msg_lo(NM);
+    std::vector<int32_t> msg_pair(NM), msg_src(NM), msg_dstnode(NM);
+    for (int64_t i = 0; i < NM; i++) {
+        const Msg &mg = msgs[sorder[i]];
+        gs_off[i + 1] = gs_off[i] + (mg.hi - mg.lo);
+        msg_pair[i] = mg.pair;
+        msg_src[i] = mg.src;
+        msg_dstnode[i] = ND.dst[mg.pair];
+        msg_gr[i] = gr_off[sorder[i]];
+        msg_lo[i] = mg.lo;
+    }
+    P->n_gs = gs_off[NM];
     if (P->n_gs >= (1ll << 30))
         throw NapError{NAPSPMV_ERR_UNSUPPORTED, "g_send beyond 2^30 values"};
     {
         HostList &In = P->lists[L_INTER];
         In = HostList();
-        In.m = M;
+        In.m = NM;
         In.total = P->n_gs;
-        In.src.resize(M);
-        In.dst.resize(M);
+        In.src.resize(NM);
+        In.dst.resize(NM);
         In.ptr = gs_off;
-        for (int64_t i = 0; i < M; i++) {
-            In.src[i] = psrc[sorder[i]];
-            In.dst[i] = pdst[sorder[i]];
+        for (int64_t i = 0; i < NM; i++) {
+            In.src[i] = msgs[sorder[i]].src;
+            In.dst[i] = msgs[sorder[i]].dst;
         }
+    }
+    // per pair, its pieces in position order: first position, receiver and
+    // g_recv offset (for the off-node receive entries' unpack sources)
+    std::vector<int64_t> piece_lo(NM), piece_gr(NM);
+    std::vector<int32_t> piece_dst(NM);
+    for (int64_t q = 0; q < NM; q++) {
+        piece_lo[q] = msgs[q].lo;
+        piece_gr[q] = gr_off[q];
+        piece_dst[q] = msgs[q].dst;
     }
     std::vector<int32_t> node_ptr32(M + 1);
     for (int64_t k = 0; k <= M; k++) node_ptr32[k] = (int32_t)ND.ptr[k];
     dvec<int64_t> d_gs_off;
     d_gs_off.p = upload(gs_off);
     dvec<int32_t> d_msg_pair, d_msg_src, d_node_ptr;
-    d_msg_pair.p = upload(sorder);
+    d_msg_pair.p = upload(msg_pair);
     d_msg_src.p = upload(msg_src);
     d_node_ptr.p = upload(node_ptr32);
-    dvec<int64_t> d_pair_gr_off;
-    d_pair_gr_off.p = upload(pair_gr_off);
+    dvec<int64_t> d_msg_gr, d_msg_lo;
+    d_msg_gr.p = upload(msg_gr);
+    d_msg_lo.p = upload(msg_lo);
 
     const int64_t ngs = P->n_gs;
     dvec<int32_t> msg_of(ngs);
@@ -866,10 +1049,10 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
     if (ngs) {
         CK(cudaMalloc(&P->lists[L_INTER].d_idx, sizeof(int32_t) * ngs));
         CK(cudaMalloc(&P->d_xfer_dst, sizeof(int32_t) * ngs));
-        k_fill_gsend<<<blocks_for(ngs), 256>>>(ngs, d_gs_off.p, M, d_msg_pair.p, d_msg_src.p,
-                                              d_pair_gr_off.p, d_node_ptr.p, ND.d_idx, part, rb,
-                                              jb, P->lists[L_INTER].d_idx, P->d_xfer_dst,
-                                              msg_of.p, j0key.p);
+        k_fill_gsend<<<blocks_for(ngs), 256>>>(ngs, d_gs_off.p, NM, d_msg_pair.p, d_msg_src.p,
+                                              d_msg_gr.p, d_msg_lo.p, d_node_ptr.p, ND.d_idx,
+                                              part, rb, jb, P->lists[L_INTER].d_idx,
+                                              P->d_xfer_dst, msg_of.p, j0key.p);
         CK(cudaGetLastError());
     }
 
@@ -917,15 +1100,19 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
     for (int64_t k = 0; k < M; k++) pair_key[k] = ((uint64_t)ND.src[k] << nb) | ND.dst[k];
     dvec<uint64_t> d_pair_key;
     d_pair_key.p = upload(pair_key);
-    dvec<int32_t> d_recv_proc;
-    d_recv_proc.p = upload(P->recv_proc);
+    dvec<int64_t> d_pair_piece, d_piece_lo, d_piece_gr;
+    dvec<int32_t> d_piece_dst;
+    d_pair_piece.p = upload(pair_piece);
+    d_piece_lo.p = upload(piece_lo);
+    d_piece_gr.p = upload(piece_gr);
+    d_piece_dst.p = upload(piece_dst);
     dvec<uint64_t> j1key(nbnl), j1alt(nbnl);
     if (nbnl) {
         CK(cudaMalloc(&P->d_unp_src, sizeof(int32_t) * nbnl));
         k_unpack_src<<<blocks_for(nbnl), 256>>>(nbnl, bnl_keys.p, jb, part, ppn, nb, M,
-                                               d_pair_key.p, d_recv_proc.p, d_pair_gr_off.p,
-                                               d_node_ptr.p, ND.d_idx, rb, j1key.p,
-                                               P->d_unp_src, bad.p);
+                                               d_pair_key.p, d_pair_piece.p, d_piece_lo.p,
+                                               d_piece_dst.p, d_piece_gr.p, d_node_ptr.p,
+                                               ND.d_idx, rb, j1key.p, P->d_unp_src, bad.p);
         CK(cudaGetLastError());
         check_bad(bad, "internal: off-node column without a node-pair message");
     }
@@ -1019,7 +1206,7 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
         int64_t i = 0;
         for (int32_t x = 0; x <= nn; x++) {
             int64_t first_rank = (int64_t)x * ppn;
-            while (i < M && msg_src[i] < first_rank) i++;
+            while (i < NM && msg_src[i] < first_rank) i++;
             P->node_gs[x] = gs_off[i];
         }
     }
@@ -1029,10 +1216,16 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
         P->h_rowptr.resize(n + 1);
         for (int64_t i = 0; i <= n; i++) P->h_rowptr[i] = (int32_t)h[i];
     }
+    // sliced-row copies of the whole matrix and of its two split parts
+    build_sell(P, 0, P->h_rowptr, P->d_rowptr, P->d_colenc, P->d_val, P->d_val32, part);
+    build_sell(P, 1, P->h_rowptrL, P->d_rowptrL, P->d_colL, P->d_valL, P->d_val32L, part);
+    build_sell(P, 2, P->h_rowptrR, P->d_rowptrR, P->d_colR, P->d_valR, P->d_val32R, part);
+    CK(cudaDeviceSynchronize());
+
     P->gs_msg_off = gs_off;
     P->gs_msg_dstnode = msg_dstnode;
-    std::vector<int32_t> gs_off32(M + 1);
-    for (int64_t i = 0; i <= M; i++) gs_off32[i] = (int32_t)gs_off[i];
+    std::vector<int32_t> gs_off32(NM + 1);
+    for (int64_t i = 0; i <= NM; i++) gs_off32[i] = (int32_t)gs_off[i];
     P->d_gs_msg_off = upload(gs_off32);
     P->d_gs_msg_dstnode = upload(msg_dstnode);
 
@@ -1065,6 +1258,11 @@ void plan_free(napspmv_plan_t *P)
     if (P->ev_join) cudaEventDestroy(P->ev_join);
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (auto &S : P->sell) {
+        void *sp[] = {S.d_info, S.d_perm, S.d_col, S.d_val, S.d_val32, S.d_long};
+        for (void *p : sp)
+            if (p) cudaFree(p);
+    }
     delete P;
     cudaSetDevice(cur);
 }
@@ -1087,12 +1285,13 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         return NAPSPMV_ERR_ARG;
     }
     if (flags & ~(NAPSPMV_F32_VALUES | NAPSPMV_MAP_TEXT | NAPSPMV_PARTITION_STRIDED |
-                  NAPSPMV_MAP_MAJORITY | NAPSPMV_COMPOSED_GATHERS)) {
+                  NAPSPMV_MAP_MAJORITY | NAPSPMV_COMPOSED_GATHERS | NAPSPMV_MAP_SPLIT)) {
         set_error(NAPSPMV_ERR_ARG, "unknown plan flag");
         return NAPSPMV_ERR_ARG;
     }
-    if ((flags & NAPSPMV_MAP_MAJORITY) && (flags & NAPSPMV_MAP_TEXT)) {
-        set_error(NAPSPMV_ERR_ARG, "NAPSPMV_MAP_MAJORITY and NAPSPMV_MAP_TEXT exclude each other");
+    if ((flags & NAPSPMV_MAP_MAJORITY) && (flags & (NAPSPMV_MAP_TEXT | NAPSPMV_MAP_SPLIT))) {
+        set_error(NAPSPMV_ERR_ARG, "NAPSPMV_MAP_MAJORITY excludes NAPSPMV_MAP_TEXT and "
+                                   "NAPSPMV_MAP_SPLIT");
         return NAPSPMV_ERR_ARG;
     }
     if (A->n >= (1ll << 30) || A->nnz >= (1ll << 31) - 64) {
@@ -1114,30 +1313,34 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         int rc = ws_alloc(P, P->ws);
         if (rc) throw NapError{rc, "workspace allocation failed"};
         P->ws->owned_by_plan = true;
-        // defaults: lanes per row from the mean row length
+        // defaults, measured on GB300 (FP64, per apply):
+        //  - rows of more than 12 stored entries on average: the phased engine
+        //    with the sliced rows (one lane per row, no shared-memory stage,
+        //    chunk groups dealt round robin).  2^23-row banded random workload:
+        //    1.71 ms, against 2.18 ms overlapped with sliced rows and 2.00 ms
+        //    overlapped with two-lane warp tiles (its SpMV step alone: 0.72 ms
+        //    against 1.04 ms);
+        //  - shorter rows (the stencils): the overlapped engine with CTA tiles,
+        //    one lane per row, 512 rows / 1536 entries (3D 7-point 128^3: 76 us,
+        //    against 79 us phased and 89 us overlapped with sliced rows).
+        // The lane count and tile shape serve the CTA and warp pipelines when an
+        // apply asks for them: one lane per row keeps exactly one FP64 FMA per
+        // stored entry (GB300's FP64 pipe is the scarce unit); longer rows take
+        // more lanes, with 1024-row / 2048-entry tiles.
         double avg = (double)P->nnz / (double)P->n;
-        // rows are summed from shared memory; one lane per row keeps exactly one
-        // FP64 FMA per stored entry (GB300's FP64 pipe is the scarce unit).
-        // (measured: two stages of 1536 entries beat 2048 on the 2^21-row 7-point
-        // and the 2^22-row 9-point workloads, and deeper pipelines, which cost
-        // CTAs per SM)
         int vec = avg <= 16 ? 1 : avg <= 32 ? 2 : avg <= 96 ? 4 : avg <= 384 ? 16 : 32;
         int rows = 512 / vec;
         int cap = 1536;
         int ctas = 0;  // occupancy maximum
-        int pipeline = NAPSPMV_PIPELINE_CTA;
-        // several lanes per row: the gathers dominate and want L1.  Measured on
-        // the 2^23-row banded random workload (about 20 entries per row):
-        // 1024-row / 2048-entry CTA tiles split into warp tiles, three CTAs per
-        // SM (the fourth CTA's shared memory leaves the gathers too little L1)
+        const bool sell = P->sell[0].slots >= 0 && avg > 12;
+        int pipeline = sell ? NAPSPMV_PIPELINE_SELL : NAPSPMV_PIPELINE_CTA;
+        int engine = sell ? NAPSPMV_ENGINE_PHASED : NAPSPMV_ENGINE_OVERLAP;
         if (vec > 1) {
             rows = 1024;
             cap = 2048;
-            ctas = 3;
-            pipeline = NAPSPMV_PIPELINE_WARP;
         }
         P->defaults.precision = NAPSPMV_PREC_F64;
-        P->defaults.engine = NAPSPMV_ENGINE_OVERLAP;
+        P->defaults.engine = engine;
         P->defaults.vec = vec;
         P->defaults.ctas_per_sm = ctas;
         P->defaults.chunk = 4096;

@@ -473,7 +473,9 @@ int slot_apply(int32_t count, const napspmv_cg_slot *slots, bool from_x, int32_t
     // plan takes 77 us phased against 191 us in the persistent launch, a
     // 0.4M-row one 33 against 70 us; below about half a million entries the
     // shared launch costs less than a call per slot.  The choice depends on the
-    // slot's own matrix only, so a slot's bits do not depend on the batch.
+    // slot's own matrix only, and every slot runs with its own plan's default
+    // options (slots whose defaults differ go into separate fused launches), so
+    // a slot's bits do not depend on the batch.
     int nb = 0;
     for (int i = 0; i < count; i++) {
         if (plans[i]->nnz >= NAPSPMV_SOLO_NNZ) {
@@ -491,7 +493,7 @@ int slot_apply(int32_t count, const napspmv_cg_slot *slots, bool from_x, int32_t
         }
     }
     if (nb == 0) return NAPSPMV_OK;
-    napspmv_opts o = plans[0]->defaults;
+    napspmv_opts o{};  // unset fields: each slot's own plan defaults
     o.precision = precision;
     o.engine = NAPSPMV_ENGINE_FUSED;
     return apply_batch(nb, plans, wss, vs, ws_, reps, sc, &o, st);

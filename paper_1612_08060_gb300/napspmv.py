@@ -17,10 +17,10 @@ LIB_PATH = os.path.join(HERE, "libnapspmv.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 HOST, DEVICE = 0, 1
-F32_VALUES, MAP_TEXT, PARTITION_STRIDED, MAP_MAJORITY, COMPOSED_GATHERS = 1, 2, 4, 8, 16
+F32_VALUES, MAP_TEXT, PARTITION_STRIDED, MAP_MAJORITY, COMPOSED_GATHERS, MAP_SPLIT = 1, 2, 4, 8, 16, 32
 PREC_F64, PREC_F32 = 0, 1
 ENGINE_DEFAULT, ENGINE_FUSED, ENGINE_PHASED, ENGINE_OVERLAP = 0, 1, 2, 3
-PIPELINE_CTA, PIPELINE_WARP = 1, 2
+PIPELINE_CTA, PIPELINE_WARP, PIPELINE_SELL = 1, 2, 3
 HALO_ON, HALO_OFF = 1, 2
 SOLO_NNZ = 1 << 19  # NAPSPMV_SOLO_NNZ
 (LIST_STD, LIST_NODE, LIST_INTER, LIST_J0, LIST_J1, LIST_J2, LIST_BLL, LIST_BNL, LIST_LBUF,

@@ -1,5 +1,5 @@
 """Seeded random draws of matrix and launch options (engine, precision, lanes
-per row, CTA or warp tiles, tile shape, staged receive buffers, chain length,
+per row, CTA, warp or sliced-row tiles, tile shape, staged receive buffers, chain length,
 partition flags): every apply matches the oracle within the FP64 bound, or the
 oracle's FP32-value product within 1e-13 in FP32 mode."""
 import numpy as np
@@ -40,7 +40,7 @@ def _draws(count=60, seed=4242):
             eng = nap.ENGINE_OVERLAP
         prec = int(rng.choice([nap.PREC_F64, nap.PREC_F32]))
         opts = dict(engine=eng, precision=prec, vec=int(rng.choice([1, 2, 4, 8, 16, 32])),
-                    pipeline=int(rng.choice([nap.PIPELINE_CTA, nap.PIPELINE_WARP])),
+                    pipeline=int(rng.choice([nap.PIPELINE_CTA, nap.PIPELINE_WARP, nap.PIPELINE_SELL])),
                     tile_nnz=int(rng.choice([64, 256, 1536])),
                     tile_rows=int(rng.choice([8, 64, 512])),
                     halo=int(rng.choice([nap.HALO_ON, nap.HALO_OFF])))

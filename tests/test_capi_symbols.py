@@ -74,9 +74,10 @@ def test_limits_and_flags_rejected_before_device_work(libpath):
     assert plan(3, 0, 4, 2) == nap.ERR_ARG          # n_p > N
     assert plan(3, 0, 0, 2) == nap.ERR_ARG          # n_p < 1
     assert plan(3, 0, 2, 0) == nap.ERR_ARG          # ppn < 1
-    assert plan(3, 0, 2, 1, 32) == nap.ERR_ARG      # unknown flag bit
+    assert plan(3, 0, 2, 1, 64) == nap.ERR_ARG      # unknown flag bit
     assert plan(3, 0, 2, 1, nap.MAP_TEXT | nap.MAP_MAJORITY) == nap.ERR_ARG
-    assert b"exclude each other" in nap.lib().napspmv_last_error()
+    assert b"excludes" in nap.lib().napspmv_last_error()
+    assert plan(3, 0, 2, 1, nap.MAP_SPLIT | nap.MAP_MAJORITY) == nap.ERR_ARG
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
@@ -99,6 +100,7 @@ def test_binding_constants_match_the_header():
     pairs = {"F32_VALUES": "NAPSPMV_F32_VALUES", "MAP_TEXT": "NAPSPMV_MAP_TEXT",
              "PARTITION_STRIDED": "NAPSPMV_PARTITION_STRIDED",
              "MAP_MAJORITY": "NAPSPMV_MAP_MAJORITY", "COMPOSED_GATHERS": "NAPSPMV_COMPOSED_GATHERS",
+             "MAP_SPLIT": "NAPSPMV_MAP_SPLIT", "PIPELINE_SELL": "NAPSPMV_PIPELINE_SELL",
              "ENGINE_FUSED": "NAPSPMV_ENGINE_FUSED", "ENGINE_PHASED": "NAPSPMV_ENGINE_PHASED",
              "ENGINE_OVERLAP": "NAPSPMV_ENGINE_OVERLAP", "PIPELINE_CTA": "NAPSPMV_PIPELINE_CTA",
              "PIPELINE_WARP": "NAPSPMV_PIPELINE_WARP", "HALO_ON": "NAPSPMV_HALO_ON",

@@ -88,6 +88,37 @@ def test_majority_mapping_workloads(cfg, scale):
                        O.OraclePlan(A.row_ptr, A.col, w.n_p, w.ppn, flags=O.MAP_MAJORITY))
 
 
+@pytest.mark.parametrize("n,dens,seed,n_p,ppn", CASES[::2])
+@pytest.mark.parametrize("extra", [0, 1])
+def test_split_mapping(n, dens, seed, n_p, ppn, extra):
+    """Node splitting (NAPSPMV_MAP_SPLIT, the text after Eq. U), alone and with
+    the prose's receive order or the strided partition: bit-exact against the
+    oracle."""
+    A = I.random_pattern(n, dens, seed)
+    gx, ox = [(nap.MAP_TEXT, O.MAP_TEXT), (nap.PARTITION_STRIDED, O.STRIDED)][extra]
+    assert_plans_equal(gpu_plan(A, n_p, ppn, nap.MAP_SPLIT | gx),
+                       O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=O.MAP_SPLIT | ox))
+
+
+@pytest.mark.parametrize("cfg,scale", [(1, 1), (2, 1), (3, 1), (4, 64)])
+def test_split_mapping_workloads(cfg, scale):
+    """Node splitting on the workloads, bit-exact against the oracle at full
+    size.  In the 3D 7-point 128^3 and the Q1 2048^2 workloads an inner node has
+    2 partner nodes and 16 processes (groups of 8 on both sides: 8 messages per
+    pair); the first and the last node have one partner (a group of 16: the 4
+    pairs that touch them carry 16 messages each)."""
+    w = I.workload(cfg, scale)
+    A = w.build()
+    gp = gpu_plan(A, w.n_p, w.ppn, nap.MAP_SPLIT)
+    op = O.OraclePlan(A.row_ptr, A.col, w.n_p, w.ppn, flags=O.MAP_SPLIT)
+    assert_plans_equal(gp, op)
+    if cfg in (2, 3):
+        plain = O.OraclePlan(A.row_ptr, A.col, w.n_p, w.ppn).stats()
+        st = op.stats()
+        assert st["nap_inter_vals"] == plain["nap_inter_vals"]
+        assert st["nap_inter_msgs"] == 8 * (plain["nap_inter_msgs"] - 4) + 16 * 4
+
+
 def test_empty_matrix_and_empty_rows():
     n = 50
     A = I.CSR(np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.zeros(0))
@@ -130,7 +161,7 @@ def test_config3_full_size_counts():
 def test_invalid_inputs_rejected():
     A = I.poisson2d(8)
     with pytest.raises(nap.NapError) as e:
-        nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, 32)  # unknown flag bit
+        nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, 64)  # unknown flag bit
     assert e.value.code == nap.ERR_ARG
     with pytest.raises(nap.NapError) as e:
         nap.napspmv_plan(A.row_ptr, A.col, A.val, 4, 2, nap.MAP_MAJORITY | nap.MAP_TEXT)
