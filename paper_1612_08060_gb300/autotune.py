@@ -27,7 +27,7 @@ CANDIDATES = {
     "tile_nnz": [1024, 1536, 2048, 3072],
     "tile_rows": [256, 384, 512, 1024],
     "stages": [2, 3],
-    "pipeline": [nap.PIPELINE_CTA, nap.PIPELINE_WARP],
+    "pipeline": [nap.PIPELINE_SELL, nap.PIPELINE_CTA, nap.PIPELINE_WARP],
     "ctas_per_sm": [0, 2, 3, 4],
     "chunk": [2048, 4096, 8192],
 }
@@ -58,6 +58,26 @@ def time_opts(plan, v, w, opts, reps=20, trials=3, stream=None):
     if nap.napspmv_status(plan, s) != 0:
         return float("inf")
     return best  # ms per apply
+
+
+def _load(cache_file):
+    if cache_file and os.path.exists(cache_file):
+        for k, v in json.load(open(cache_file)).items():
+            _cache.setdefault(k, v)
+
+
+def apply_cached(plan, row_ptr, precision=nap.PREC_F64, cache_file=None):
+    """Install the tuned options cached for this matrix key (in memory or in
+    `cache_file`) as the plan's defaults, without measuring anything; returns
+    them, or None when the matrix was never tuned."""
+    key = matrix_key(row_ptr, plan.n_p, plan.ppn, precision)
+    if key not in _cache:
+        _load(cache_file)
+    if key not in _cache:
+        return None
+    best = dict(_cache[key]["opts"])
+    nap.napspmv_set_default_opts(plan, nap.make_opts(precision=precision, **best))
+    return best
 
 
 def tune(plan, row_ptr, precision=nap.PREC_F64, reps=20, max_sweeps=2, cache_file=None,

@@ -1,42 +1,47 @@
 """Continuous-batching request server for node-aware SpMV and CG-IR solves.
 
 Requests (an SpMV, or a CG solve to ||b - A x|| <= rtol ||b|| with FP32-stored
-values inside FP64 iterative refinement) arrive over time on Poisson matrices of
-differing size.  The server:
+values inside FP64 iterative refinement) arrive over time on matrices of
+differing size: Poisson matrices named by a generator spec (``dim``, ``side``)
+or the caller's own CSR (``matrix``, with ``n_p``, ``ppn`` and an optional
+cache ``key``) and right-hand side (``rhs``).  The server:
 
 * admits an arrived request when a slot is free (at most ``max_active`` in
-  flight) and its device memory fits the budget; plans (built on first use) stay
-  resident in an LRU cache, evicted only when unused and memory is short;
-* every step launches one batched fused apply for all SpMV requests, one batched
-  CG-residual step (FP64 values) for the solves entering an outer iteration, and
-  ``iters_per_step`` batched CG iterations (FP32 values) for the solves in their
-  inner loop, so the work of all admitted requests overlaps on the device.
-  Requests on a matrix of at least ``SOLO_NNZ`` stored entries take their
-  products on the phased engine, one call each, where a product costs less than
-  its share of the fused launch (the batched CG calls route their slots the
-  same way);
-* reads every solve's scalars with one device-to-host copy per step, retires
-  finished requests and stamps their latency (completion - arrival).
+  flight) and its device memory fits the budget; plans (built on first use, with
+  the autotuner's cached launch options for that matrix when a tuning cache is
+  given) stay resident in an LRU cache, evicted only when unused and memory is
+  short;
+* keeps the admitted requests in two groups served in turn: while the GPU runs
+  one group's step, the host reads the other group's scalars (one device-to-host
+  copy per step, awaited on its own event), retires what finished and queues
+  that group's next step, so the device never idles on a host decision;
+* a step launches one batched fused apply for the group's SpMV requests, one
+  batched CG-residual step (FP64 values) for the solves entering an outer
+  iteration and ``iters_per_step`` batched CG iterations (FP32 values) for the
+  solves in their inner loop.  Requests on a matrix of at least ``SOLO_NNZ``
+  stored entries take their products (and their CG steps) on the phased engine,
+  on a second stream, so they overlap the fused launch.
 
-Each request's arithmetic is independent of what else is in flight (fixed
-per-row and per-slot reduction orders), so a request served alone and in a mix
-gives the same bits.  This holds while the matrices that share a fused launch
-have the same default launch options, as all of the served Poisson matrices do
-(one lane per row): a fused launch takes its first plan's options.  ``max_active=1`` is the plain per-request loop (same
-kernels, same plan cache, one request at a time in arrival order).
+Each request's arithmetic is independent of what else is in flight: a fixed
+engine per request (the fused engine with its own plan's options, or the phased
+engine on a large matrix), fixed per-row and per-slot reduction orders and the
+same sequence of steps whatever its group holds, so a request served alone and
+in a mix gives the same bits.  ``max_active=1`` is the plain per-request loop
+(same kernels, same plan cache, one request at a time in arrival order).
 
-PyTorch provides device memory and the stream; all compute is in libnapspmv.
+PyTorch provides device memory and the streams; all compute is in libnapspmv.
 """
 from __future__ import annotations
 
 import collections
+import hashlib
 import math
 import time
 
 import numpy as np
 import torch
 
-from . import inputs
+from . import autotune, inputs
 from . import napspmv as nap
 
 
@@ -73,7 +78,7 @@ class Request:
 class Server:
     def __init__(self, mem_budget=None, max_active=64, iters_per_step=8, rtol=1e-10,
                  inner_rtol=1e-4, max_outer=40, max_inner=200000, device=None, keep_results=False,
-                 cache=None):
+                 cache=None, tune_cache=None):
         self.dev = torch.device(device or "cuda")
         free, _ = torch.cuda.mem_get_info(self.dev)
         self.budget = int(mem_budget if mem_budget else 0.5 * free)
@@ -82,8 +87,14 @@ class Server:
         self.rtol, self.inner_rtol = rtol, inner_rtol
         self.max_outer, self.max_inner = max_outer, max_inner
         self.keep = keep_results
-        self.stream = torch.cuda.Stream(self.dev)
+        self.stream = torch.cuda.Stream(self.dev)       # fused launches and CG kernels
+        self.solo_stream = torch.cuda.Stream(self.dev)  # products on large matrices
         self.solo_opts = nap.make_opts(engine=nap.ENGINE_PHASED)
+        # unset fields: each plan's own defaults (one launch per option set)
+        self.fused_opts = nap.make_opts(engine=nap.ENGINE_FUSED)
+        self.tune_cache = tune_cache
+        self.hbuf = [torch.zeros(max_active, 2, 8, dtype=torch.float64).pin_memory()
+                     for _ in range(2)]
         # plans may be shared between servers (a warm cache): their bytes are
         # then counted by whoever built them
         self.cache: "collections.OrderedDict[str, Matrix]" = (
@@ -93,14 +104,31 @@ class Server:
         self.batch_sizes = []
 
     # ------------------------------------------------------------ matrices
+    @staticmethod
+    def _key(spec):
+        if "matrix" in spec:
+            if spec.get("key"):
+                return f"user_{spec['key']}_np{spec['n_p']}_ppn{spec['ppn']}"
+            A = spec["matrix"]
+            h = hashlib.sha256()
+            for arr in (A.row_ptr, A.col, A.val):
+                h.update(np.ascontiguousarray(arr).tobytes())
+            return f"user_{h.hexdigest()[:24]}_np{spec['n_p']}_ppn{spec['ppn']}"
+        return f"{spec['dim']}d_{spec['side']}_np{spec['n_p']}_ppn{spec['ppn']}"
+
     def _matrix(self, spec):
-        key = f"{spec['dim']}d_{spec['side']}_np{spec['n_p']}_ppn{spec['ppn']}"
+        key = self._key(spec)
         if key in self.cache:
             self.cache.move_to_end(key)
             return self.cache[key]
-        A = inputs.poisson2d(spec["side"]) if spec["dim"] == 2 else inputs.poisson3d(spec["side"])
+        if "matrix" in spec:
+            A = spec["matrix"]
+        else:
+            A = inputs.poisson2d(spec["side"]) if spec["dim"] == 2 else inputs.poisson3d(spec["side"])
         with torch.cuda.stream(self.stream):
             m = Matrix(key, A, spec["n_p"], spec["ppn"])
+            if self.tune_cache:
+                autotune.apply_cached(m.plan, A.row_ptr, nap.PREC_F64, cache_file=self.tune_cache)
         self.cache[key] = m
         self.mem_used += m.plan_bytes
         return m
@@ -135,7 +163,8 @@ class Server:
         d = self.dev
         with torch.cuda.stream(self.stream):
             r.ws = nap.Workspace(m.plan)
-            rhs = torch.from_numpy(inputs.vector(n, spec["seed"])).to(d, non_blocking=True)
+            host_rhs = spec["rhs"] if "rhs" in spec else inputs.vector(n, spec["seed"])
+            rhs = torch.from_numpy(np.ascontiguousarray(host_rhs, np.float64)).to(d, non_blocking=True)
             if r.kind == "spmv":
                 r.v = rhs
                 r.w = torch.empty(n, dtype=torch.float64, device=d)
@@ -170,35 +199,61 @@ class Server:
     def _chunks(xs, k=64):
         return [xs[i:i + k] for i in range(0, len(xs), k)]
 
-    def _step(self, active):
-        s = self.stream
-        spmv = [r for r in active if r.state == "spmv"]
-        outer = [r for r in active if r.state == "outer"]
-        inner = [r for r in active if r.state == "inner"]
-        self.batch_sizes.append(len(active))
+    def _enqueue(self, g, reqs):
+        """Queue one step of a group's work; returns (event, solves whose
+        scalars the event's copy brings back)."""
+        s, s2 = self.stream, self.solo_stream
+        spmv = [r for r in reqs if r.state == "spmv"]
+        outer = [r for r in reqs if r.state == "outer"]
+        inner = [r for r in reqs if r.state == "inner"]
+        self.batch_sizes.append(len(reqs))
+        solo = [r for r in reqs if r.m.solo]
+        if solo:
+            # the second stream starts after everything queued so far (the
+            # requests' inputs and their last transitions)
+            fork = torch.cuda.Event()
+            fork.record(s)
+            s2.wait_event(fork)
+            with torch.cuda.stream(s2):
+                for r in spmv:
+                    if r.m.solo:
+                        nap.napspmv_apply_batch([r.m.plan], [r.v], [r.w], [1], opts=self.solo_opts,
+                                                ws=[r.ws], stream=s2)
+                for grp in self._chunks([r for r in outer if r.m.solo]):
+                    nap.napspmv_cg_batch_init([r.outer_slot for r in grp], nap.PREC_F64, stream=s2)
+                for grp in self._chunks([r for r in inner if r.m.solo]):
+                    nap.napspmv_cg_batch_iterate([r.inner_slot for r in grp], nap.PREC_F32,
+                                                 self.iters, stream=s2)
+                join = torch.cuda.Event()
+                join.record(s2)
         with torch.cuda.stream(s):
-            for r in spmv:
-                if r.m.solo:
-                    nap.napspmv_apply_batch([r.m.plan], [r.v], [r.w], [1], opts=self.solo_opts,
-                                            ws=[r.ws], stream=s)
             for grp in self._chunks([r for r in spmv if not r.m.solo]):
                 nap.napspmv_apply_batch([r.m.plan for r in grp], [r.v for r in grp],
-                                        [r.w for r in grp], [1] * len(grp),
+                                        [r.w for r in grp], [1] * len(grp), opts=self.fused_opts,
                                         ws=[r.ws for r in grp], stream=s)
-            for grp in self._chunks(outer):
+            for grp in self._chunks([r for r in outer if not r.m.solo]):
                 nap.napspmv_cg_batch_init([r.outer_slot for r in grp], nap.PREC_F64, stream=s)
-            for grp in self._chunks(inner):
+            for grp in self._chunks([r for r in inner if not r.m.solo]):
                 nap.napspmv_cg_batch_iterate([r.inner_slot for r in grp], nap.PREC_F32,
                                              self.iters, stream=s)
+            if solo:
+                s.wait_event(join)
             cg = outer + inner
-            host = None
             if cg:
-                host = torch.stack([r.scal for r in cg]).cpu().numpy()  # one copy, synchronises
-            else:
-                s.synchronize()
+                self.hbuf[g][:len(cg)].copy_(torch.stack([r.scal for r in cg]), non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return ev, cg
+
+    def _finish(self, g, reqs, ev, cg):
+        """Wait for a group's step, retire what finished and queue the state
+        transitions of its solves (before the group's next step)."""
+        ev.synchronize()
         now = time.perf_counter()
-        for r in spmv:
-            self._retire(r, now)
+        host = self.hbuf[g][:len(cg)].numpy() if cg else None
+        for r in reqs:
+            if r.state == "spmv":
+                self._retire(r, now)
         to_inner, to_outer = [], []
         for q, r in enumerate(cg):
             sc = host[q]
@@ -215,6 +270,7 @@ class Server:
                 if math.sqrt(max(rr, 0.0)) <= self.inner_rtol * math.sqrt(max(bb, 1e-300)) \
                         or r.inner >= self.max_inner or not math.isfinite(rr):
                     to_outer.append(r)
+        s = self.stream
         with torch.cuda.stream(s):
             for grp in self._chunks(to_inner):
                 nap.napspmv_cg_batch_init([r.inner_slot for r in grp], nap.PREC_F32,
@@ -228,34 +284,48 @@ class Server:
             r.outer += 1
         self.steps += 1
 
+    @staticmethod
+    def _chunks(xs, k=64):
+        return [xs[i:i + k] for i in range(0, len(xs), k)]
+
     # ------------------------------------------------------------ driver
     def run(self, specs, realtime=True):
-        """Serve `specs` (dicts from inputs.serving_requests).  With realtime,
-        request q becomes visible at t0 + arrival; otherwise all are queued at
-        once.  Returns the list of finished Request objects."""
+        """Serve `specs` (dicts from inputs.serving_requests, or caller specs
+        with ``matrix`` / ``rhs``).  With realtime, request q becomes visible at
+        t0 + arrival; otherwise all are queued at once.  Returns the list of
+        finished Request objects."""
         reqs = [Request(s) for s in specs]
         pending = collections.deque(sorted(reqs, key=lambda r: r.arrival))
         queue: collections.deque = collections.deque()
-        active = []
+        groups = [[], []]
+        inflight = [None, None]
         t0 = time.perf_counter()
         for r in reqs:
             r.t_arrive = t0 + (r.arrival if realtime else 0.0)
-        while pending or queue or active:
+        while pending or queue or groups[0] or groups[1]:
             now = time.perf_counter()
             while pending and pending[0].t_arrive <= now:
                 queue.append(pending.popleft())
-            while queue and len(active) < self.max_active:
+            while queue and len(groups[0]) + len(groups[1]) < self.max_active:
                 if not self._admit(queue[0]):
                     break
-                active.append(queue.popleft())
-            if not active:
+                g = 0 if len(groups[0]) <= len(groups[1]) else 1
+                groups[g].append(queue.popleft())
+            if not groups[0] and not groups[1]:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].t_arrive - time.perf_counter())))
                     continue
                 if queue:
                     raise RuntimeError("request does not fit the memory budget")
-            self._step(active)
-            active = [r for r in active if r.state != "done"]
+            for g in (0, 1):
+                if inflight[g] is not None:
+                    ev, cg, stepped = inflight[g]
+                    self._finish(g, stepped, ev, cg)
+                    inflight[g] = None
+                    groups[g] = [r for r in groups[g] if r.state != "done"]
+                if groups[g]:
+                    ev, cg = self._enqueue(g, groups[g])
+                    inflight[g] = (ev, cg, list(groups[g]))
         return reqs
 
 

@@ -75,3 +75,55 @@ def test_solo_matrices_alone_equals_mix():
         else:
             res = rhs - O.spmv(A.row_ptr, A.col, A.val, r.result)
             assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(rhs), r.id
+
+
+def test_caller_matrices_and_vectors(tmp_path):
+    """Requests may carry the caller's own CSR and right-hand side (here banded
+    random matrices with about 20 entries per row, whose plans default to two
+    lanes per row for the tile pipelines, beside a Poisson spec): the results
+    are the same bits alone and in a mix, SpMV within the oracle's bound, CG-IR
+    to 1e-10; a tuning cache entry for a matrix is installed on its plan."""
+    import json
+    from paper_1612_08060_gb300 import autotune, napspmv as nap, serve
+    mats = [I.banded_random(2500, 21), I.banded_random(3500, 22)]
+    # make the banded matrices symmetric positive definite for the CG requests
+    spd = []
+    for A in mats:
+        d = A.to_dense()
+        d = 0.5 * (d + d.T)
+        d[np.arange(A.n), np.arange(A.n)] = 1.0 + np.abs(d).sum(axis=1) - np.abs(np.diag(d))
+        rows, cols = np.nonzero(d)
+        rp = np.zeros(A.n + 1, np.int64)
+        np.cumsum(np.bincount(rows, minlength=A.n), out=rp[1:])
+        spd.append(I.CSR(rp, cols.astype(np.int32), d[rows, cols]))
+    specs = []
+    for q in range(10):
+        A = spd[q % 2]
+        specs.append(dict(id=q, arrival=0.0003 * q, kind="spmv" if q % 3 else "cg", n=A.n,
+                          matrix=A, n_p=6 + q % 2, ppn=2, key=f"m{q % 2}",
+                          rhs=I.vector(A.n, 50 + q)))
+    specs.append(dict(_specs(1, seed=3)[0], id=10))
+    cache = str(tmp_path / "tune.json")
+    key = autotune.matrix_key(spd[0].row_ptr, 6, 2, nap.PREC_F64)
+    opts = {"engine": nap.ENGINE_OVERLAP, "vec": 2, "tile_nnz": 1024, "tile_rows": 256,
+            "stages": 2, "pipeline": nap.PIPELINE_SELL, "ctas_per_sm": 0, "chunk": 2048}
+    with open(cache, "w") as f:
+        json.dump({key: {"opts": opts, "ms": 1.0}}, f)
+    srv = serve.Server(max_active=64, keep_results=True, tune_cache=cache)
+    mixed = srv.run(specs, realtime=True)
+    d = nap.napspmv_get_default_opts(srv.cache["user_m0_np6_ppn2"].plan)
+    assert (d.tile_nnz, d.tile_rows, d.chunk) == (1024, 256, 2048)
+    alone = serve.Server(max_active=1, keep_results=True, tune_cache=cache).run(specs,
+                                                                                  realtime=False)
+    by_id = {r.id: r for r in alone}
+    for r in mixed:
+        assert np.array_equal(r.result, by_id[r.id].result), r.id
+        if "matrix" not in r.spec:
+            continue
+        A, rhs = r.spec["matrix"], r.spec["rhs"]
+        if r.kind == "spmv":
+            ref = O.spmv(A.row_ptr, A.col, A.val, rhs)
+            assert np.linalg.norm(r.result - ref) <= 1e-13 * np.linalg.norm(ref)
+        else:
+            res = rhs - O.spmv(A.row_ptr, A.col, A.val, r.result)
+            assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(rhs), r.id
