@@ -147,9 +147,19 @@ def ncu_record(workload, what):
     return d.get("records", {}).get(f"{workload}|{what}")
 
 
-def build_workload(cfg):
+def build_workload(cfg, rows=0):
+    """Workload `cfg` (inputs.workload).  rows > 0 with cfg 4: the banded random
+    structure at that many rows, with the 2^23-row workload's absolute band
+    (+-41,943 columns), 1,024 rows per process and ppn 32 (a smaller case of the
+    same kernels, for profiling)."""
     from paper_1612_08060_gb300 import inputs
-    w = inputs.workload(cfg)
+    if rows and cfg == 4:
+        band = 41943.0 / rows
+        w = inputs.Workload(f"banded_random_N{rows}_band41943_np{rows // 1024}_ppn32",
+                            max(1, rows // 1024), 32, 1238,
+                            lambda: inputs.banded_random(rows, 1238, band=band))
+    else:
+        w = inputs.workload(cfg)
     A = w.build()
     v = inputs.vector(A.n, w.seed)
     return w, A, v
@@ -564,6 +574,9 @@ def main():
     ap.add_argument("--serve-sweep", default="",
                     help="comma-separated further loads (fractions of the plain loop's "
                          "saturated throughput), e.g. 0.5,1.0,1.2")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="with --config 4 and --profile-spmv: the banded random structure at "
+                         "this many rows (same band, rows per process and ppn)")
     ap.add_argument("--profile-spmv", type=int, default=0,
                     help="profiling mode: one apply, then this many SpMV-step launches; "
                          "prints nothing")
@@ -587,7 +600,7 @@ def main():
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
     if args.profile_spmv:
-        w, A, v = build_workload(args.config)
+        w, A, v = build_workload(args.config, args.rows)
         plan = nap.napspmv_plan(A.row_ptr, A.col, A.val, w.n_p, w.ppn, nap.F32_VALUES)
         opts = make_opts(nap, args, args.precision)
         stream = torch.cuda.Stream(device=dev)

@@ -261,20 +261,22 @@ int napspmv_spmv_step(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, doub
 int napspmv_apply_host(napspmv_plan_t *P, const double *v_host, double *w_host, int32_t reps,
                        double scale, void *stream);
 
-/* One persistent launch over `count` independent applies (each with its own
+/* Persistent launches over `count` independent applies (each with its own
  * plan, workspace, vectors, reps and scale): the batched form used by the
  * request server.  ws[i] may be NULL only if no other entry uses the same
- * plan's own workspace.  count <= 64.  Fused engine (count = 1 runs as
- * napspmv_apply_ex with the given options), so with count > 1 plans built
- * with NAPSPMV_PARTITION_STRIDED give ERR_UNSUPPORTED.  Errors stay per
- * entry: an entry whose wait times out sets its workspace's error flag
- * (napspmv_ws_status) and its remaining work is skipped; the other entries
- * complete.  Options: the fields of `opts` left 0 (or opts NULL) take the
- * defaults of plans[0], for every entry (one kernel, one lane count per row).
- * Each entry's result is bit-identical to napspmv_apply_ex of its plan with
- * those resolved options; with its own plan's defaults instead (another lane
- * count where rows average more than 16 entries), an FP64 row sum may round
- * in another order. */
+ * plan's own workspace.  count <= 64; all plans on one device.  count = 1
+ * runs as napspmv_apply_ex with the given options; count > 1 runs on the
+ * fused engine, whatever engine `opts` names.  Options: each entry resolves
+ * the fields of `opts` left 0 (or opts NULL) against its own plan's
+ * defaults.  Entries whose resolved launch options agree share one fused
+ * launch; the launches are issued on `stream` in order of each option set's
+ * first entry.  Each entry's result is bit-identical to napspmv_apply_ex of
+ * its plan on the fused engine with its resolved options, whatever else is
+ * in the batch.  Errors stay per entry: an entry whose wait times out sets
+ * its workspace's error flag (napspmv_ws_status) and its remaining work is
+ * skipped; the other entries complete.  An invalid entry (NULL vector,
+ * reps < 1, a shared workspace, options its plan cannot run) fails the whole
+ * call before anything is launched. */
 int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const *ws,
                         const double *const *v, double *const *w, const int32_t *reps,
                         const double *scale, const napspmv_opts *opts, void *stream);
@@ -294,14 +296,12 @@ int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_
  *     the counters are cleared by each call.  Calls that overlap on the GPU
  *     (on different streams, or on different plans) race on it: order them.
  *   - The first call on a device looks the array's device address up (with
- *     that device current); make that first call before any stream capture.
- *     The address is cached for the life of the process: it does not survive
- *     cudaDeviceReset on that device.
+ *     that device current) and caches it for the life of the process: the
+ *     cached address does not survive cudaDeviceReset on that device.
  *   - Scratch needed: counters + b_{l->l} + b_{l->nl} + 2 g_send + b_{nl->l}
  *     values, plus N for the chain vector when reps > 1.
  *   - Uses the fused engine with the plan's current work items and FP64
- *     values (strided plans: ERR_UNSUPPORTED); device-side timeouts are
- *     reported by napspmv_status(P). */
+ *     values; device-side timeouts are reported by napspmv_status(P). */
 int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double *w, int32_t reps,
                           double scale, void *stream);
 

@@ -1153,30 +1153,32 @@ __device__ __forceinline__ void sell_chunk(const SellView &S, int c, const XT *x
     }
 }
 
-// Chunks are handed out in groups of kSellGroup consecutive chunks (one per
-// warp of a CTA), group g to CTA g mod grid: every CTA sweeps the arrays
+// Chunks are handed out in groups of W consecutive chunks (one per warp of a
+// CTA of W warps), group g to CTA g mod grid: every CTA sweeps the arrays
 // together with the others, so the pages in use at any time stay few.
 // Measured on the 2^23-row banded random workload (FP64): contiguous runs of
 // chunks per CTA, which spread ~900 CTAs over 3.4 GB of matrix and receive
 // buffers, took 1.42 ms; groups of 8 handed out this way, 0.70 ms.  Four
 // entries per step suit short rows (the stencils), eight longer ones.
+// kSellGroup: the group of the 8-warp CTAs (the fused engine's).
 constexpr int kSellGroup = 8;
 
-template <bool F32, int MODE, int U>
-__global__ void __launch_bounds__(NT, U >= 8 ? 4 : 6)
+template <bool F32, int MODE, int U, int W = 8>
+__global__ void __launch_bounds__(32 * W, W == 8 ? (U >= 8 ? 4 : 6) : 1)
     k_spmv_s(SellView S, const void *xs, const void *blls, const void *bnls, double *y, float *y32,
              Scale sc, int *err)
 {
     using XT = typename std::conditional<F32, float, double>::type;
+    constexpr int WPB = W, G = W;
     const XT *x = static_cast<const XT *>(xs), *bll = static_cast<const XT *>(blls),
              *bnl = static_cast<const XT *>(bnls);
     griddep_wait();
     if (*(volatile const int *)err) return;  // sticky error: no work until cleared
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t pol = policy_evict_first();  // the matrix streams once per apply
-    const int ngroups = (S.nch + kSellGroup - 1) / kSellGroup;
+    const int ngroups = (S.nch + G - 1) / G;
     for (int g = blockIdx.x; g < ngroups; g += gridDim.x)
-        for (int c = g * kSellGroup + warp; c < min(S.nch, (g + 1) * kSellGroup); c += WPB)
+        for (int c = g * G + warp; c < min(S.nch, (g + 1) * G); c += WPB)
             sell_chunk<F32, false, MODE, U>(S, c, x, bll, bnl, y, y32, sc, lane, pol);
     // rows longer than kSellLong: a warp each
     const int gw = blockIdx.x * WPB + warp, nw = gridDim.x * WPB;
@@ -1858,16 +1860,23 @@ static HaloKernel pick_halo(int vec)
 
 using SellKernel = void (*)(SellView, const void *, const void *, const void *, double *, float *,
                             Scale, int *);
-template <bool F32, int U>
+template <bool F32, int U, int W = 8>
 static SellKernel pick_sell_u(int mode)
 {
-    return mode == kLocal ? k_spmv_s<F32, kLocal, U>
-                          : mode == kRemote ? k_spmv_s<F32, kRemote, U> : k_spmv_s<F32, kFull, U>;
+    return mode == kLocal ? k_spmv_s<F32, kLocal, U, W>
+                          : mode == kRemote ? k_spmv_s<F32, kRemote, U, W> : k_spmv_s<F32, kFull, U, W>;
 }
+
+// Rows of more than 12 entries (unroll 8): CTAs of 32 warps, one per SM, that
+// sweep one process's 32 chunks at a time, so that the SM's L1 (no shared
+// memory) holds that process's receive window.  Measured on the 2^23-row
+// banded random workload: 680 against 735 us (FP64), 490 against 570 us (FP32
+// values) for 8-warp CTAs on four processes per SM; the stencils' short rows
+// run best with 8-warp CTAs.
 template <bool F32>
 static SellKernel pick_sell(int mode, int unroll)
 {
-    return unroll == 8 ? pick_sell_u<F32, 8>(mode) : pick_sell_u<F32, 4>(mode);
+    return unroll == 8 ? pick_sell_u<F32, 8, 32>(mode) : pick_sell_u<F32, 4, 8>(mode);
 }
 
 struct SpmvLaunch {
@@ -1875,6 +1884,7 @@ struct SpmvLaunch {
     HaloKernel hfn = nullptr;  // set: the remote pass with staged receive buffers
     SellKernel sfn = nullptr;  // set: the sliced-row pass
     SellView S{};
+    int sw = 8;  // warps per CTA of the sliced-row pass
     Csr3 A{};
     const Item *tiles = nullptr;
     const int32_t *bll_rank = nullptr, *bnl_rank = nullptr;
@@ -1927,10 +1937,11 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
         // no shared memory: the whole unified L1 / shared storage is L1
         NAP_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
         int occ = 0;
-        NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf, NT, 0));
+        L.sw = sell_unroll(P) == 8 ? 32 : 8;
+        NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf, 32 * L.sw, 0));
         if (o.ctas_per_sm > 0) occ = std::min(occ, o.ctas_per_sm);
-        const int64_t ctas = std::max<int64_t>((SP.nch + kSellGroup - 1) / kSellGroup,
-                                               (SP.n_long + WPB - 1) / WPB);
+        const int64_t ctas = std::max<int64_t>((SP.nch + L.sw - 1) / L.sw,
+                                               (SP.n_long + L.sw - 1) / L.sw);
         L.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)P->num_sms * std::max(occ, 1)));
         if (mode == kLocal)  // leave one CTA slot per SM for the message steps
             L.grid = (int)std::max<int64_t>(
@@ -2029,9 +2040,19 @@ static void launch_pdl(bool pdl, void (*kern)(KArgs...), int grid, size_t smem, 
 static void spmv_run(const SpmvLaunch &L, const void *x, const napspmv_ws_t *ws, double *y,
                      float *y32, double scale, int stages, cudaStream_t s, bool pdl)
 {
-    if (L.sfn)
-        launch_pdl(pdl, L.sfn, L.grid, 0, s, L.S, x, (const void *)ws->bll, (const void *)ws->bnl,
-                   y, y32, make_scale(scale), ws->err);
+    if (L.sfn) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)L.grid);
+        cfg.blockDim = dim3((unsigned)(32 * L.sw));
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = pdl ? 1 : 0;
+        (void)cudaLaunchKernelEx(&cfg, L.sfn, L.S, x, (const void *)ws->bll, (const void *)ws->bnl,
+                                 y, y32, make_scale(scale), ws->err);
+    }
     else if (L.hfn)
         launch_pdl(pdl, L.hfn, L.grid, L.sm, s, L.A, (const void *)ws->bll, (const void *)ws->bnl,
                    y, y32, make_scale(scale), L.tiles, L.n, L.cap, L.rows, stages, L.bll_rank,
@@ -2322,6 +2343,9 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
             break;
         }
         oi[i] = resolve_opts(P, opts);
+        // several entries share fused launches, whatever engine the options name:
+        // validate them for that engine
+        if (count > 1) oi[i].engine = NAPSPMV_ENGINE_FUSED;
         if ((rc = check_opts(P, oi[i]))) break;
         if ((rc = build_items(P, oi[i].chunk, oi[i].tile_rows, oi[i].tile_nnz))) break;
         for (int q = 0; q < i; q++) {
