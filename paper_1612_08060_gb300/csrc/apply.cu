@@ -1211,6 +1211,16 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? (U >= 8 ? 4 : 6) : 1)
 // never runs; its wait is bounded all the same.
 constexpr int kFusedChunk = NT * 8;
 constexpr int kLevels = 4;
+// Elements per thread per pass in the message levels, and sliced-row entries
+// per step in level 3, whatever the row lengths.  With these the kernel fits
+// its 64 registers (4 CTAs per SM) without spilling.  Measured per apply on
+// GB300 (3D 7-point 128^3 / Q1 2048^2 / 2^23-row banded random, FP64):
+// 8 elements and 4 (8 for the long rows of the banded matrix) entries took
+// 124 / 223 / 2,058 us; 4 elements 106 / 200 / 1,881 us; 2 elements with 4
+// entries for every matrix 106 / 199 / 1,633 us.  Three elements per thread
+// at 6 CTAs per SM (40 registers) spilled and ran slower on every workload.
+constexpr int kFusedU = 2;
+constexpr int kFusedSellU = 4;
 
 struct FJob {
     SellView F;                   // the whole matrix, sliced rows
@@ -1299,7 +1309,7 @@ __device__ __noinline__ void step_pack_transfer(double *gsend, double *grecv, co
                                                 const int32_t *dst, int b, int e, int tid)
 {
     const uint64_t pol = policy_evict_first();
-    constexpr int U = 8;
+    constexpr int U = kFusedU;
     for (int base = b + tid; base < e; base += NT * U) {
         uint32_t sv[U];
         int32_t dv[U];
@@ -1336,7 +1346,7 @@ __device__ __noinline__ void step_pack_transfer(double *gsend, double *grecv, co
 }
 
 // One unit of level `lvl` of job J (see the level list above).
-template <bool F32, int U>
+template <bool F32>
 __device__ __forceinline__ void fused_unit(const FJob &J, int lvl, int u, const double *x, double *y,
                                            int tid)
 {
@@ -1348,10 +1358,10 @@ __device__ __forceinline__ void fused_unit(const FJob &J, int lvl, int u, const 
         case 0: {
             const int nu0 = (J.n0 + kFusedChunk - 1) / kFusedChunk;
             if (u < nu0) {
-                step_gather<true, 8>(J.bll, x, J.src0, b, min(J.n0, b + kFusedChunk), tid);
+                step_gather<true, kFusedU>(J.bll, x, J.src0, b, min(J.n0, b + kFusedChunk), tid);
             } else {
                 const int b1 = (u - nu0) * kFusedChunk;
-                step_gather<true, 8>(J.composed ? J.bnl : J.lbuf, x, J.src1, b1,
+                step_gather<true, kFusedU>(J.composed ? J.bnl : J.lbuf, x, J.src1, b1,
                                      min(J.n1, b1 + kFusedChunk), tid);
             }
             break;
@@ -1361,7 +1371,7 @@ __device__ __forceinline__ void fused_unit(const FJob &J, int lvl, int u, const 
                                min(J.n_gs, b + kFusedChunk), tid);
             break;
         default:
-            step_gather<true, 8>(J.bnl, J.grecv, J.unp_src, b, min(J.n_bnl, b + kFusedChunk), tid);
+            step_gather<true, kFusedU>(J.bnl, J.grecv, J.unp_src, b, min(J.n_bnl, b + kFusedChunk), tid);
             break;
         }
         return;
@@ -1371,7 +1381,8 @@ __device__ __forceinline__ void fused_unit(const FJob &J, int lvl, int u, const 
     const int ng = (J.F.nch + kSellGroup - 1) / kSellGroup;
     if (u < ng) {
         for (int c = u * kSellGroup + warp; c < min(J.F.nch, (u + 1) * kSellGroup); c += WPB)
-            sell_chunk<F32, true, kFull, U>(J.F, c, x, J.bll, J.bnl, y, nullptr, J.scale, lane, pol);
+            sell_chunk<F32, true, kFull, kFusedSellU>(J.F, c, x, J.bll, J.bnl, y, nullptr, J.scale,
+                                                      lane, pol);
     } else {
         const int q = (u - ng) * WPB + warp;
         if (q < J.F.n_long)
@@ -1379,7 +1390,7 @@ __device__ __forceinline__ void fused_unit(const FJob &J, int lvl, int u, const 
     }
 }
 
-template <bool F32, int U, int MAXJ>
+template <bool F32, int MAXJ>
 __global__ void __launch_bounds__(NT, 4) k_fused(const __grid_constant__ FusedParams<MAXJ> prm)
 {
     const int tid = threadIdx.x;
@@ -1408,9 +1419,9 @@ __global__ void __launch_bounds__(NT, 4) k_fused(const __grid_constant__ FusedPa
                 double *y = (((J.reps - 1 - k) & 1) == 0) ? J.w : J.xtmp;
                 const int base = prm.off[lvl][j];
                 // units u with (base + u) mod grid == this CTA
-                int u = (int)(((long long)blockIdx.x - base) % g);
+                int u = (int)blockIdx.x - base % g;
                 if (u < 0) u += g;
-                for (; u < J.nunits[lvl]; u += g) fused_unit<F32, U>(J, lvl, u, x, y, tid);
+                for (; u < J.nunits[lvl]; u += g) fused_unit<F32>(J, lvl, u, x, y, tid);
             }
             if (!grid_barrier(prm)) return;
         }
@@ -1421,11 +1432,7 @@ __global__ void __launch_bounds__(NT, 4) k_fused(const __grid_constant__ FusedPa
 template <int MAXJ>
 struct FusedKernelTable {
     using Fn = void (*)(const FusedParams<MAXJ>);
-    static Fn get(int unroll, bool f32)
-    {
-        if (unroll == 8) return f32 ? k_fused<true, 8, MAXJ> : k_fused<false, 8, MAXJ>;
-        return f32 ? k_fused<true, 4, MAXJ> : k_fused<false, 4, MAXJ>;
-    }
+    static Fn get(bool f32) { return f32 ? k_fused<true, MAXJ> : k_fused<false, MAXJ>; }
 };
 
 static bool valid_vec(int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; }
@@ -1791,7 +1798,7 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
     prm.bar = reinterpret_cast<unsigned int *>(w0->ctr);
     prm.stallctr = w0->ctr + 1;
     NAP_CUDA(cudaMemsetAsync(w0->ctr, 0, 2 * sizeof(unsigned long long), s));
-    auto fn = FusedKernelTable<MAXJ>::get(sell_unroll(plans[0]), f32);
+    auto fn = FusedKernelTable<MAXJ>::get(f32);
     NAP_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
     int occ = 0;
     NAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, NT, 0));
@@ -2063,6 +2070,21 @@ static void spmv_run(const SpmvLaunch &L, const void *x, const napspmv_ws_t *ws,
                    stages, ws->err);
 }
 
+// CTAs of a message-step kernel that the whole GPU holds at once.  These
+// kernels stride over their elements, so their grid is one wave: a CTA that
+// waited for a slot would start its share only when another CTA ended.  The
+// FP64 kernels hold 40 registers a thread, so 6 CTAs of 256 threads fit an
+// SM, not 8; one wave of 6 per SM took the 2^23-row banded random apply from
+// 1.65 to 1.59 ms.
+template <class... A>
+static int64_t one_wave(const napspmv_plan_t *P, void (*kern)(A...))
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    return (int64_t)P->num_sms * occ;
+}
+
 // The four message steps of one apply (phases 1-4) as kernels on stream s;
 // returns the number of launches.  The later steps are launched as
 // programmatic dependents of the earlier ones; pdl_first: the first step too.
@@ -2070,27 +2092,29 @@ template <class T>
 static int64_t enqueue_messages(const napspmv_plan_t *P, const T *x, T *bll, T *lbuf, T *gsend,
                                 T *grecv, T *bnl, int *err, cudaStream_t s, bool pdl_first)
 {
-    auto grid = [&](int64_t n) {
-        return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
-                                                            (int64_t)P->num_sms * 8));
+    auto grid = [&](int64_t n, int64_t wave) {
+        return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8), wave));
     };
     int64_t nk = 0;
     if (P->n_bll + P->n_lbuf > 0) {
-        launch_pdl(pdl_first, k_gather2<T>, grid(P->n_bll + P->n_lbuf), 0, s, x,
+        launch_pdl(pdl_first, k_gather2<T>,
+                   grid(P->n_bll + P->n_lbuf, one_wave(P, k_gather2<T>)), 0, s, x,
                    (const int32_t *)P->lists[L_BLL].d_idx, bll, (int)P->n_bll,
                    (const int32_t *)P->lists[L_LBUF].d_idx, lbuf, (int)P->n_lbuf,
                    (const int *)err);
         nk++;
     }
     if (P->n_gs > 0) {
-        launch_pdl(true, k_pack<T>, grid(P->n_gs), 0, s, x, (const T *)lbuf,
+        launch_pdl(true, k_pack<T>, grid(P->n_gs, one_wave(P, k_pack<T>)), 0, s, x, (const T *)lbuf,
                    (const uint32_t *)P->d_pack_src, gsend, (int)P->n_gs, (const int *)err);
-        launch_pdl(true, k_transfer<T>, grid(P->n_gs), 0, s, (const T *)gsend,
+        launch_pdl(true, k_transfer<T>, grid(P->n_gs, one_wave(P, k_transfer<T>)), 0, s,
+                   (const T *)gsend,
                    (const int32_t *)P->d_xfer_dst, grecv, (int)P->n_gs, (const int *)err);
         nk += 2;
     }
     if (P->n_bnl > 0) {
-        launch_pdl(true, k_unpack<T>, grid(P->n_bnl), 0, s, (const T *)grecv,
+        launch_pdl(true, k_unpack<T>, grid(P->n_bnl, one_wave(P, k_unpack<T>)), 0, s,
+                   (const T *)grecv,
                    (const int32_t *)P->d_unp_src, bnl, (int)P->n_bnl, (const int *)err);
         nk++;
     }
@@ -2105,8 +2129,9 @@ static int64_t enqueue_composed(const napspmv_plan_t *P, const void *x, napspmv_
 {
     const int64_t n = P->n_bll + P->n_bnl;
     if (n == 0) return 0;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
-                                                              (int64_t)P->num_sms * 8));
+    const int g = (int)std::max<int64_t>(
+        1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
+                             f32 ? one_wave(P, k_gather2<float>) : one_wave(P, k_gather2<double>)));
     if (f32)
         launch_pdl(pdl, k_gather2<float>, g, 0, s, static_cast<const float *>(x),
                    (const int32_t *)P->lists[L_BLL].d_idx, reinterpret_cast<float *>(ws->bll),
