@@ -523,6 +523,13 @@ def e2e_host(nap, torch, dev, ctx, reps, steps, ws):
     """The same metric through the host-buffer entry point: every call copies v
     in from pinned host memory, runs `reps` chained applies and copies w out."""
     A, B, plan, stream, scale = ctx["A"], ctx["B"], ctx["plan"], ctx["stream"], ctx["scale"]
+    # the host-buffer call applies the plan's default options: make them the
+    # timed region's (its engine, precision and tiles), as the library resolves them
+    o, d = ctx["opts"], nap.napspmv_get_default_opts(plan)
+    for f, _ in type(o)._fields_:
+        if f == "precision" or getattr(o, f):
+            setattr(d, f, getattr(o, f))
+    nap.napspmv_set_default_opts(plan, d)
     vh = torch.from_numpy(ctx["v"].copy()).pin_memory()
     wh = torch.empty_like(vh).pin_memory()
     nap.napspmv_apply_host(plan, vh, wh, reps, scale, stream=stream)
