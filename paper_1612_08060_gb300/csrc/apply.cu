@@ -1071,10 +1071,9 @@ __global__ void __launch_bounds__(NT, 4)
 // registers only), and every lane of a DFMA carries an entry: the rows of a
 // chunk have similar counts.  Each row is summed in its stored order, one DFMA
 // per entry (FP32 mode: FP32 product, FP64 add): the bits of the one-lane CSR
-// kernels.  Chunks go to CTAs in contiguous runs (a CTA stays within a few
-// processes, whose receive buffers then stay in this SM's L1 / the L2), the
-// warps of a CTA interleaved.  Rows longer than kSellLong entries are summed
-// afterwards by whole warps from the CSR part.
+// kernels.  Chunks go to CTAs in groups, one chunk per warp (see k_spmv_s).
+// Rows longer than kSellLong entries are summed afterwards by whole warps from
+// the CSR part.
 struct SellView {
     const int2 *info;
     const int32_t *perm;
@@ -1949,7 +1948,15 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
         if (o.ctas_per_sm > 0) occ = std::min(occ, o.ctas_per_sm);
         const int64_t ctas = std::max<int64_t>((SP.nch + L.sw - 1) / L.sw,
                                                (SP.n_long + L.sw - 1) / L.sw);
-        L.grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)P->num_sms * std::max(occ, 1)));
+        // 32-warp CTAs on FP64 values: four waves of them, so that the SMs that
+        // finish their processes early take up others.  Per SM step on the
+        // 2^23-row banded random matrix (GB300): one wave 0.675 ms; in the
+        // chained apply one, two, four, eight waves 1.508, 1.471, 1.440, 1.450
+        // ms.  With FP32 values one wave stays best (1.011 against 1.016,
+        // 1.023, 1.051 ms).
+        const int waves = (L.sw == 32 && !f32) ? 4 : 1;
+        L.grid = (int)std::max<int64_t>(
+            1, std::min<int64_t>(ctas, (int64_t)P->num_sms * std::max(occ, 1) * waves));
         if (mode == kLocal)  // leave one CTA slot per SM for the message steps
             L.grid = (int)std::max<int64_t>(
                 1, std::min<int64_t>(ctas, (int64_t)P->num_sms * std::max(occ - 1, 1)));
@@ -2070,12 +2077,8 @@ static void spmv_run(const SpmvLaunch &L, const void *x, const napspmv_ws_t *ws,
                    stages, ws->err);
 }
 
-// CTAs of a message-step kernel that the whole GPU holds at once.  These
-// kernels stride over their elements, so their grid is one wave: a CTA that
-// waited for a slot would start its share only when another CTA ended.  The
-// FP64 kernels hold 40 registers a thread, so 6 CTAs of 256 threads fit an
-// SM, not 8; one wave of 6 per SM took the 2^23-row banded random apply from
-// 1.65 to 1.59 ms.
+// CTAs of a message-step kernel that the whole GPU holds at once (the FP64
+// kernels hold 40 registers a thread: 6 CTAs of 256 threads per SM).
 template <class... A>
 static int64_t one_wave(const napspmv_plan_t *P, void (*kern)(A...))
 {
@@ -2085,6 +2088,24 @@ static int64_t one_wave(const napspmv_plan_t *P, void (*kern)(A...))
     return (int64_t)P->num_sms * occ;
 }
 
+// Grid of a message-step kernel over n elements, in chunks of NT * 8 (each
+// CTA strides over chunk b, b + grid, ...).  Up to four resident waves' worth
+// of chunks: one wave, so that no CTA waits for a slot and then runs its share
+// alone at the end.  More chunks than that: 96 CTAs per SM, many waves, whose
+// CTAs the hardware starts as others end, so that the SMs stay full to the
+// last chunk.  Measured per apply on GB300 (2^23-row banded random, FP64 /
+// FP32 values; 3D 7-point 128^3): 8 CTAs per SM (1.3 waves) 1.654 ms; one
+// wave 1.609 / 1.070 ms, 75.3 us; 16, 32, 64, 96 and 128 CTAs per SM 1.558,
+// 1.530, 1.511, 1.505, 1.508 / 1.048, 1.029, 1.016, 1.010, 1.011 ms; one
+// chunk per CTA 1.527 / 1.061 ms.  The 128^3 workload stays within four waves
+// (75.9 us with one chunk per CTA).
+static int msg_grid(const napspmv_plan_t *P, int64_t n, int64_t wave)
+{
+    const int64_t chunks = (n + NT * 8 - 1) / (NT * 8);
+    const int64_t g = chunks <= 4 * wave ? wave : (int64_t)P->num_sms * 96;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, g));
+}
+
 // The four message steps of one apply (phases 1-4) as kernels on stream s;
 // returns the number of launches.  The later steps are launched as
 // programmatic dependents of the earlier ones; pdl_first: the first step too.
@@ -2092,9 +2113,7 @@ template <class T>
 static int64_t enqueue_messages(const napspmv_plan_t *P, const T *x, T *bll, T *lbuf, T *gsend,
                                 T *grecv, T *bnl, int *err, cudaStream_t s, bool pdl_first)
 {
-    auto grid = [&](int64_t n, int64_t wave) {
-        return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8), wave));
-    };
+    auto grid = [&](int64_t n, int64_t wave) { return msg_grid(P, n, wave); };
     int64_t nk = 0;
     if (P->n_bll + P->n_lbuf > 0) {
         launch_pdl(pdl_first, k_gather2<T>,
@@ -2129,9 +2148,7 @@ static int64_t enqueue_composed(const napspmv_plan_t *P, const void *x, napspmv_
 {
     const int64_t n = P->n_bll + P->n_bnl;
     if (n == 0) return 0;
-    const int g = (int)std::max<int64_t>(
-        1, std::min<int64_t>((n + NT * 8 - 1) / (NT * 8),
-                             f32 ? one_wave(P, k_gather2<float>) : one_wave(P, k_gather2<double>)));
+    const int g = msg_grid(P, n, f32 ? one_wave(P, k_gather2<float>) : one_wave(P, k_gather2<double>));
     if (f32)
         launch_pdl(pdl, k_gather2<float>, g, 0, s, static_cast<const float *>(x),
                    (const int32_t *)P->lists[L_BLL].d_idx, reinterpret_cast<float *>(ws->bll),
