@@ -1948,13 +1948,18 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
         if (o.ctas_per_sm > 0) occ = std::min(occ, o.ctas_per_sm);
         const int64_t ctas = std::max<int64_t>((SP.nch + L.sw - 1) / L.sw,
                                                (SP.n_long + L.sw - 1) / L.sw);
-        // 32-warp CTAs on FP64 values: four waves of them, so that the SMs that
-        // finish their processes early take up others.  Per SM step on the
-        // 2^23-row banded random matrix (GB300): one wave 0.675 ms; in the
-        // chained apply one, two, four, eight waves 1.508, 1.471, 1.440, 1.450
-        // ms.  With FP32 values one wave stays best (1.011 against 1.016,
-        // 1.023, 1.051 ms).
-        const int waves = (L.sw == 32 && !f32) ? 4 : 1;
+        // 32-warp CTAs on FP64 values: up to four waves of them, so that the SMs
+        // that finish their processes early take up others, while every CTA
+        // keeps at least 13 groups.  On GB300, 2^23-row banded random matrix
+        // (8,192 groups): the chained apply with one, two, four, eight waves
+        // took 1.508, 1.471, 1.440, 1.450 ms, and the SM step 0.675 ms with one
+        // wave, 0.601 with four.  At 2^21 rows (2,048 groups) four waves were
+        // slower than one (169 against 159 us).  With FP32 values one wave
+        // stays best (1.011 against 1.016, 1.023, 1.051 ms per apply).
+        const int64_t slots = (int64_t)P->num_sms * std::max(occ, 1);
+        const int waves = (L.sw == 32 && !f32)
+                              ? (int)std::max<int64_t>(1, std::min<int64_t>(4, ctas / (slots * 13)))
+                              : 1;
         L.grid = (int)std::max<int64_t>(
             1, std::min<int64_t>(ctas, (int64_t)P->num_sms * std::max(occ, 1) * waves));
         if (mode == kLocal)  // leave one CTA slot per SM for the message steps
