@@ -487,9 +487,13 @@ def measure(nap, torch, dev, args, cfg, precision, reps, steps, warmup, ws=1, wi
                      "peak_kind": peak_kind, "traffic": spmv_traffic,
                      "kernel": "the three-block SpMV step (one launch = every row of one apply)",
                      "timing": f"CUDA events around {sp_n} back-to-back napspmv_spmv_step launches "
-                               "on the benchmark stream after the timed region; inside it the "
-                               "overlapped engine runs the same rows as a local and a remote "
-                               "launch",
+                               "on the benchmark stream after the timed region" + (
+                                   "; inside it the overlapped engine runs the same rows as a "
+                                   "local and a remote launch" if engine == nap.ENGINE_OVERLAP
+                                   else "; inside it the phased engine runs the same launch"
+                                   if engine == nap.ENGINE_PHASED
+                                   else "; inside it the fused kernel's last level sums the "
+                                   "same rows"),
                      "algorithmic_bytes": B_spmv, "launch_ms": round(spmv_ms, 5)},
         "step_roofline": {"bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
                           "frac": round(achieved / peak, 4),
