@@ -321,14 +321,25 @@ int napspmv_cg_ir(napspmv_plan_t *P, const double *b, double *x, double rtol, do
 // Batched CG steps over independent requests (the request server).
 //
 // Every slot is one CG solve with its own plan, vectors and scalars.  A dot
-// product of slot i always uses kSlotBlocks blocks over a fixed strided
-// partition of its own vectors and a fixed-order final sum, so its value
-// does not depend on which other slots share the launch.
+// product of slot i uses slot_blocks(n_i) blocks over a fixed strided
+// partition of its own vectors and a fixed-order final sum: a function of its
+// own length only, so its value does not depend on which other slots share
+// the launch.  One block per 1,024 elements, at most 4,096; the final sum is
+// one warp's, lanes over a fixed stride and a fixed shuffle tree.  A fixed 64
+// blocks left a 1.7M-element solve latency-bound on its vector kernels (about
+// 330 us per CG iteration on GB300).
 namespace nap {
 namespace {
 
 constexpr int kMaxSlots = 64;
-constexpr int kSlotBlocks = 64;
+constexpr int kSlotBlocksMax = 4096;
+constexpr int64_t kSlotChunk = 4 * 256;
+
+__host__ __device__ __forceinline__ int slot_blocks(int64_t n)
+{
+    const int64_t b = (n + kSlotChunk - 1) / kSlotChunk;
+    return (int)(b < 1 ? 1 : (b > kSlotBlocksMax ? kSlotBlocksMax : b));
+}
 
 enum Scl { S_RR = 0, S_PQ = 1, S_ALPHA = 2, S_BETA = 3, S_RRNEW = 4, S_BB = 5 };
 
@@ -355,13 +366,15 @@ __global__ void __launch_bounds__(kThreads) k_slot_vec(const __grid_constant__ S
     __shared__ double sh[kThreads / 32];
     const int i = blockIdx.y;
     const int64_t n = S.n[i];
+    const int nb = slot_blocks(n);
+    if ((int)blockIdx.x >= nb) return;  // the whole block: this slot needs fewer
     const double *b = S.b[i];
     double *x = S.x[i], *r = S.r[i], *p = S.p[i], *q = S.q[i];
     const double alpha = mode == 2 ? S.scal[i][S_ALPHA] : 0.0;
     const double beta = mode == 3 ? S.scal[i][S_BETA] : 0.0;
     double s1 = 0.0, s2 = 0.0;
     for (int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x; k < n;
-         k += (int64_t)kSlotBlocks * kThreads) {
+         k += (int64_t)nb * kThreads) {
         if (mode == 0 || mode == 4) {
             const double v = mode == 0 ? b[k] - q[k] : b[k];
             r[k] = v;
@@ -384,21 +397,27 @@ __global__ void __launch_bounds__(kThreads) k_slot_vec(const __grid_constant__ S
     s1 = block_sum_any(s1, sh);
     if (mode == 0 || mode == 4) s2 = block_sum_any(s2, sh);
     if (threadIdx.x == 0) {
-        partial[(i * kSlotBlocks + blockIdx.x) * 2 + 0] = s1;
-        partial[(i * kSlotBlocks + blockIdx.x) * 2 + 1] = s2;
+        partial[((int64_t)i * kSlotBlocksMax + blockIdx.x) * 2 + 0] = s1;
+        partial[((int64_t)i * kSlotBlocksMax + blockIdx.x) * 2 + 1] = s2;
     }
 }
 
-// Fixed-order sums of the partials and the scalar recurrences of CG.
+// Fixed-order sums of the partials (lane l adds partials l, l + 32, ... in
+// order, then a fixed shuffle tree) and the scalar recurrences of CG.
 __global__ void k_slot_final(const __grid_constant__ SlotVecs S, int mode, const double *partial)
 {
-    const int i = blockIdx.x;
-    if (threadIdx.x != 0) return;
+    const int i = blockIdx.x, lane = threadIdx.x;
     double a = 0.0, c = 0.0;
-    for (int q = 0; q < kSlotBlocks; q++) {
-        a += partial[(i * kSlotBlocks + q) * 2 + 0];
-        c += partial[(i * kSlotBlocks + q) * 2 + 1];
+    const int nb = slot_blocks(S.n[i]);
+    for (int q = lane; q < nb; q += 32) {
+        a += partial[((int64_t)i * kSlotBlocksMax + q) * 2 + 0];
+        c += partial[((int64_t)i * kSlotBlocksMax + q) * 2 + 1];
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane != 0) return;
     double *s = S.scal[i];
     if (mode == 0 || mode == 4) {
         s[S_RR] = a;
@@ -415,7 +434,9 @@ __global__ void k_slot_final(const __grid_constant__ SlotVecs S, int mode, const
 
 int slot_vec(const SlotVecs &S, int mode, double *partial, cudaStream_t st)
 {
-    k_slot_vec<<<dim3(kSlotBlocks, S.count), kThreads, 0, st>>>(S, mode, partial);
+    int gx = 1;
+    for (int i = 0; i < S.count; i++) gx = std::max(gx, slot_blocks(S.n[i]));
+    k_slot_vec<<<dim3(gx, S.count), kThreads, 0, st>>>(S, mode, partial);
     count_launch(1);
     if (mode != 3) {
         k_slot_final<<<S.count, 32, 0, st>>>(S, mode, partial);
@@ -522,7 +543,7 @@ int napspmv_cg_batch_init(int32_t count, const napspmv_cg_slot *slots, int32_t p
     cudaStream_t st = (cudaStream_t)stream;
     Partials P;
     P.s = st;
-    NAP_CUDA(cudaMallocAsync(&P.p, sizeof(double) * 2 * kSlotBlocks * count, st));
+    NAP_CUDA(cudaMallocAsync(&P.p, sizeof(double) * 2 * kSlotBlocksMax * count, st));
     if (x_is_zero) return slot_vec(S, 4, P.p, st);
     if ((rc = slot_apply(count, slots, true, precision, st))) return rc;
     return slot_vec(S, 0, P.p, st);
@@ -541,7 +562,7 @@ int napspmv_cg_batch_iterate(int32_t count, const napspmv_cg_slot *slots, int32_
     cudaStream_t st = (cudaStream_t)stream;
     Partials P;
     P.s = st;
-    NAP_CUDA(cudaMallocAsync(&P.p, sizeof(double) * 2 * kSlotBlocks * count, st));
+    NAP_CUDA(cudaMallocAsync(&P.p, sizeof(double) * 2 * kSlotBlocksMax * count, st));
     for (int it = 0; it < iters; it++) {
         if ((rc = slot_apply(count, slots, false, precision, st))) return rc;
         if ((rc = slot_vec(S, 1, P.p, st))) return rc;
@@ -590,7 +611,9 @@ extern "C" int napspmv_batch_add(int32_t count, double *const *y, const double *
         A.x[i] = x[i];
         A.n[i] = n[i];
     }
-    k_slot_add<<<dim3(kSlotBlocks, count), kThreads, 0, (cudaStream_t)stream>>>(A);
+    int gx = 1;
+    for (int i = 0; i < count; i++) gx = std::max(gx, slot_blocks(n[i]));
+    k_slot_add<<<dim3(gx, count), kThreads, 0, (cudaStream_t)stream>>>(A);
     count_launch(1);
     NAP_CUDA(cudaGetLastError());
     return NAPSPMV_OK;

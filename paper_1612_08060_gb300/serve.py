@@ -11,22 +11,28 @@ cache ``key``) and right-hand side (``rhs``).  The server:
   the autotuner's cached launch options for that matrix when a tuning cache is
   given) stay resident in an LRU cache, evicted only when unused and memory is
   short;
-* keeps the admitted requests in two groups served in turn: while the GPU runs
-  one group's step, the host reads the other group's scalars (one device-to-host
-  copy per step, awaited on its own event), retires what finished and queues
-  that group's next step, so the device never idles on a host decision;
-* a step launches one batched fused apply for the group's SpMV requests, one
-  batched CG-residual step (FP64 values) for the solves entering an outer
-  iteration and ``iters_per_step`` batched CG iterations (FP32 values) for the
-  solves in their inner loop.  Requests on a matrix of at least ``SOLO_NNZ``
-  stored entries take their products (and their CG steps) on the phased engine,
-  on a second stream, so they overlap the fused launch.
+* keeps the admitted requests on matrices of fewer than ``SOLO_NNZ`` stored
+  entries in two groups served in turn: while the GPU runs one group's step,
+  the host reads the other group's scalars (one device-to-host copy per step,
+  awaited on its own event), retires what finished and queues that group's next
+  step, so the device never idles on a host decision;
+* a step of those groups launches one batched fused apply for the group's SpMV
+  requests, one batched CG-residual step (FP64 values) for the solves entering
+  an outer iteration and ``iters_per_step`` batched CG iterations (FP32 values)
+  for the solves in their inner loop;
+* keeps the requests on larger matrices in a third group on a second stream,
+  with their products on the phased engine and ``solo_iters_per_step`` CG
+  iterations per step.  That group steps on its own: the host polls its event
+  and neither kind of request waits for the other's steps.  A large 2D solve
+  needs thousands of CG iterations, and with 8 per step its host round trips,
+  not its arithmetic, set the slowest latencies.
 
 Each request's arithmetic is independent of what else is in flight: a fixed
 engine per request (the fused engine with its own plan's options, or the phased
-engine on a large matrix), fixed per-row and per-slot reduction orders and the
-same sequence of steps whatever its group holds, so a request served alone and
-in a mix gives the same bits.  ``max_active=1`` is the plain per-request loop
+engine on a large matrix), a fixed number of CG iterations per step (by its
+matrix's size), fixed per-row and per-slot reduction orders and the same
+sequence of steps whatever its group holds, so a request served alone and in a
+mix gives the same bits.  ``max_active=1`` is the plain per-request loop
 (same kernels, same plan cache, one request at a time in arrival order).
 
 PyTorch provides device memory and the streams; all compute is in libnapspmv.
@@ -75,8 +81,12 @@ class Request:
         self.result = None
 
 
+SOLO = 2  # group of the requests on large matrices
+
+
 class Server:
-    def __init__(self, mem_budget=None, max_active=64, iters_per_step=8, rtol=1e-10,
+    def __init__(self, mem_budget=None, max_active=64, iters_per_step=8,
+                 solo_iters_per_step=64, rtol=1e-10,
                  inner_rtol=1e-4, max_outer=40, max_inner=200000, device=None, keep_results=False,
                  cache=None, tune_cache=None):
         self.dev = torch.device(device or "cuda")
@@ -84,6 +94,7 @@ class Server:
         self.budget = int(mem_budget if mem_budget else 0.5 * free)
         self.max_active = max_active
         self.iters = iters_per_step
+        self.solo_iters = solo_iters_per_step
         self.rtol, self.inner_rtol = rtol, inner_rtol
         self.max_outer, self.max_inner = max_outer, max_inner
         self.keep = keep_results
@@ -94,7 +105,7 @@ class Server:
         self.fused_opts = nap.make_opts(engine=nap.ENGINE_FUSED)
         self.tune_cache = tune_cache
         self.hbuf = [torch.zeros(max_active, 2, 8, dtype=torch.float64).pin_memory()
-                     for _ in range(2)]
+                     for _ in range(3)]
         # plans may be shared between servers (a warm cache): their bytes are
         # then counted by whoever built them
         self.cache: "collections.OrderedDict[str, Matrix]" = (
@@ -161,7 +172,8 @@ class Server:
         self.mem_used += need
         n = m.n
         d = self.dev
-        with torch.cuda.stream(self.stream):
+        # the request's buffers live on the stream its steps run on
+        with torch.cuda.stream(self.solo_stream if m.solo else self.stream):
             r.ws = nap.Workspace(m.plan)
             host_rhs = spec["rhs"] if "rhs" in spec else inputs.vector(n, spec["seed"])
             rhs = torch.from_numpy(np.ascontiguousarray(host_rhs, np.float64)).to(d, non_blocking=True)
@@ -199,45 +211,37 @@ class Server:
     def _chunks(xs, k=64):
         return [xs[i:i + k] for i in range(0, len(xs), k)]
 
+    def _stream(self, g):
+        return self.solo_stream if g == SOLO else self.stream
+
+    def _iters(self, g):
+        return self.solo_iters if g == SOLO else self.iters
+
     def _enqueue(self, g, reqs):
-        """Queue one step of a group's work; returns (event, solves whose
-        scalars the event's copy brings back)."""
-        s, s2 = self.stream, self.solo_stream
+        """Queue one step of a group's work on the group's stream; returns
+        (event, solves whose scalars the event's copy brings back)."""
+        s = self._stream(g)
         spmv = [r for r in reqs if r.state == "spmv"]
         outer = [r for r in reqs if r.state == "outer"]
         inner = [r for r in reqs if r.state == "inner"]
         self.batch_sizes.append(len(reqs))
-        solo = [r for r in reqs if r.m.solo]
-        if solo:
-            # the second stream starts after everything queued so far (the
-            # requests' inputs and their last transitions)
-            fork = torch.cuda.Event()
-            fork.record(s)
-            s2.wait_event(fork)
-            with torch.cuda.stream(s2):
-                for r in spmv:
-                    if r.m.solo:
-                        nap.napspmv_apply_batch([r.m.plan], [r.v], [r.w], [1], opts=self.solo_opts,
-                                                ws=[r.ws], stream=s2)
-                for grp in self._chunks([r for r in outer if r.m.solo]):
-                    nap.napspmv_cg_batch_init([r.outer_slot for r in grp], nap.PREC_F64, stream=s2)
-                for grp in self._chunks([r for r in inner if r.m.solo]):
-                    nap.napspmv_cg_batch_iterate([r.inner_slot for r in grp], nap.PREC_F32,
-                                                 self.iters, stream=s2)
-                join = torch.cuda.Event()
-                join.record(s2)
         with torch.cuda.stream(s):
-            for grp in self._chunks([r for r in spmv if not r.m.solo]):
-                nap.napspmv_apply_batch([r.m.plan for r in grp], [r.v for r in grp],
-                                        [r.w for r in grp], [1] * len(grp), opts=self.fused_opts,
-                                        ws=[r.ws for r in grp], stream=s)
-            for grp in self._chunks([r for r in outer if not r.m.solo]):
+            if g == SOLO:
+                # one phased-engine apply each (a batch of several would share
+                # one fused launch)
+                for r in spmv:
+                    nap.napspmv_apply_batch([r.m.plan], [r.v], [r.w], [1], opts=self.solo_opts,
+                                            ws=[r.ws], stream=s)
+            else:
+                for grp in self._chunks(spmv):
+                    nap.napspmv_apply_batch([r.m.plan for r in grp], [r.v for r in grp],
+                                            [r.w for r in grp], [1] * len(grp),
+                                            opts=self.fused_opts, ws=[r.ws for r in grp], stream=s)
+            for grp in self._chunks(outer):
                 nap.napspmv_cg_batch_init([r.outer_slot for r in grp], nap.PREC_F64, stream=s)
-            for grp in self._chunks([r for r in inner if not r.m.solo]):
+            for grp in self._chunks(inner):
                 nap.napspmv_cg_batch_iterate([r.inner_slot for r in grp], nap.PREC_F32,
-                                             self.iters, stream=s)
-            if solo:
-                s.wait_event(join)
+                                             self._iters(g), stream=s)
             cg = outer + inner
             if cg:
                 self.hbuf[g][:len(cg)].copy_(torch.stack([r.scal for r in cg]), non_blocking=True)
@@ -265,12 +269,12 @@ class Server:
                 else:
                     to_inner.append(r)
             else:
-                r.inner += self.iters
+                r.inner += self._iters(g)
                 rr, bb = sc[1][0], sc[1][5]
                 if math.sqrt(max(rr, 0.0)) <= self.inner_rtol * math.sqrt(max(bb, 1e-300)) \
                         or r.inner >= self.max_inner or not math.isfinite(rr):
                     to_outer.append(r)
-        s = self.stream
+        s = self._stream(g)
         with torch.cuda.stream(s):
             for grp in self._chunks(to_inner):
                 nap.napspmv_cg_batch_init([r.inner_slot for r in grp], nap.PREC_F32,
@@ -297,35 +301,43 @@ class Server:
         reqs = [Request(s) for s in specs]
         pending = collections.deque(sorted(reqs, key=lambda r: r.arrival))
         queue: collections.deque = collections.deque()
-        groups = [[], []]
-        inflight = [None, None]
+        groups = [[], [], []]
+        inflight = [None, None, None]
         t0 = time.perf_counter()
         for r in reqs:
             r.t_arrive = t0 + (r.arrival if realtime else 0.0)
-        while pending or queue or groups[0] or groups[1]:
+        while pending or queue or any(groups):
             now = time.perf_counter()
             while pending and pending[0].t_arrive <= now:
                 queue.append(pending.popleft())
-            while queue and len(groups[0]) + len(groups[1]) < self.max_active:
+            while queue and sum(len(x) for x in groups) < self.max_active:
                 if not self._admit(queue[0]):
                     break
-                g = 0 if len(groups[0]) <= len(groups[1]) else 1
-                groups[g].append(queue.popleft())
-            if not groups[0] and not groups[1]:
+                r = queue.popleft()
+                g = SOLO if r.m.solo else (0 if len(groups[0]) <= len(groups[1]) else 1)
+                groups[g].append(r)
+            if not any(groups):
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].t_arrive - time.perf_counter())))
                     continue
                 if queue:
                     raise RuntimeError("request does not fit the memory budget")
-            for g in (0, 1):
+            progress = False
+            for g in (0, 1, SOLO):
                 if inflight[g] is not None:
                     ev, cg, stepped = inflight[g]
+                    if g == SOLO and not ev.query():
+                        continue  # the large requests' step is still running
                     self._finish(g, stepped, ev, cg)
                     inflight[g] = None
                     groups[g] = [r for r in groups[g] if r.state != "done"]
+                    progress = True
                 if groups[g]:
                     ev, cg = self._enqueue(g, groups[g])
                     inflight[g] = (ev, cg, list(groups[g]))
+                    progress = True
+            if not progress:
+                time.sleep(0.0002)
         return reqs
 
 

@@ -50,8 +50,10 @@ def test_memory_budget_admission():
 
 def test_solo_matrices_alone_equals_mix():
     """Requests on matrices of at least SOLO_NNZ entries take the phased engine
-    (SpMV and batched CG alike), the rest share the fused launch; results stay
-    the same bits served alone or in a mix, and correct."""
+    (SpMV and batched CG alike) in a group of their own on the second stream,
+    with solo_iters_per_step CG iterations a step; the rest share the fused
+    launch at iters_per_step.  Results stay the same bits served alone or in a
+    mix, and correct."""
     from paper_1612_08060_gb300 import napspmv as nap, serve
     shapes = [(3, 44, "cg"), (2, 330, "spmv"), (3, 44, "spmv"), (2, 40, "cg"), (3, 14, "spmv"),
               (2, 90, "cg"), (2, 330, "cg")]
@@ -62,10 +64,16 @@ def test_solo_matrices_alone_equals_mix():
                           n_p=max(1, round(n / 2048)), ppn=16, seed=1000 + q))
     big = [s for s in specs if _matrix(s).nnz >= nap.SOLO_NNZ]
     assert {s["kind"] for s in big} == {"spmv", "cg"} and len(big) < len(specs)
-    mixed = serve.Server(max_active=64, keep_results=True).run(specs, realtime=True)
+    srv = serve.Server(max_active=64, keep_results=True)
+    mixed = srv.run(specs, realtime=True)
     alone = serve.Server(max_active=1, keep_results=True).run(specs, realtime=False)
     by_id = {r.id: r for r in alone}
     for r in mixed:
+        if r.kind == "cg":
+            # inner iterations come in whole steps of the request's own group
+            step = srv.solo_iters if r.m.solo else srv.iters
+            assert r.inner > 0 and r.inner % step == 0, (r.id, r.inner)
+            assert r.inner == by_id[r.id].inner and r.outer == by_id[r.id].outer
         assert np.array_equal(r.result, by_id[r.id].result), r.id
         A = _matrix(r.spec)
         rhs = I.vector(A.n, r.spec["seed"])
