@@ -373,10 +373,11 @@ int napspmv_cg(napspmv_plan_t *P, const double *b, double *x, double rtol, int32
  * the right-hand side b and device vectors x, r, p, q of N values, and 8
  * device doubles of scalars: [0] r.r, [1] p.q, [2] alpha, [3] beta,
  * [4] latest r.r, [5] b.b.  Not in the paper: the batched form of the
- * request server; each slot's arithmetic does not depend on the others in
- * the call (fixed per-slot reduction order), given that the slots sharing the
- * fused launch have plans with the same default options (the launch takes the
- * first such slot's). */
+ * request server.  Each slot's arithmetic does not depend on the others in
+ * the call: its dot products use a partition fixed by its own N (one block
+ * per 1,024 values, at most 4,096) and a fixed-order final sum, and its
+ * products run with its own plan's default options (slots whose options
+ * differ go into separate fused launches). */
 /* Slots (and served SpMV requests) whose matrix holds at least this many
  * stored entries are applied on their own with the phased engine: there one
  * product costs less than its share of a fused-engine launch. */
