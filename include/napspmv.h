@@ -164,13 +164,14 @@ typedef struct {
     int32_t ctas_per_sm; /* resident CTAs per SM: the persistent CTAs of the
                             fused engine; a cap on the SpMV grid of the
                             phased / overlapped engines                       */
-    int32_t chunk;       /* gather elements per work item (fused engine)       */
+    int32_t chunk;       /* elements per message-step unit of the fused engine
+                            (32 .. 2^24; the plan default is 2048)             */
     int32_t tile_rows;   /* at most this many matrix rows per SpMV work item   */
     int32_t tile_nnz;    /* at most this many stored entries per SpMV work item
                             (staged in shared memory by bulk copies); a longer
                             single row gets a tile of its own                  */
-    int32_t stages;      /* shared-memory stages of the phased SpMV pipeline
-                            (2..4; the fused engine always uses 2)             */
+    int32_t stages;      /* shared-memory stages of the CTA and warp tile
+                            pipelines (2..4)                                   */
     int32_t pipeline;    /* SpMV tiles of the phased / overlapped engines:
                             NAPSPMV_PIPELINE_CTA (a CTA per tile),
                             NAPSPMV_PIPELINE_WARP (each warp its own stages and
@@ -179,8 +180,9 @@ typedef struct {
                             or NAPSPMV_PIPELINE_SELL (sliced rows, above)     */
     int32_t halo;        /* NAPSPMV_HALO_ON / _OFF (overlapped engine)         */
     int32_t timeout_ms;  /* limit of every device-side wait                    */
-    int32_t debug_stall; /* test hook (fused engine): 1 makes the first work
-                            item wait on a counter nothing increments, so the
+    int32_t debug_stall; /* test hook (fused engine): 1 makes the CTA of job
+                            0's first unit wait on a counter nothing
+                            increments, so the
                             launch ends with NAPSPMV_ERR_TIMEOUT after
                             timeout_ms.  After any device-side error every
                             kernel of the workspace skips its work until
@@ -243,7 +245,7 @@ int napspmv_apply_n(napspmv_plan_t *P, const double *v, double *w, int32_t reps,
 
 /* As napspmv_apply_n with explicit options (NULL = defaults) and workspace
  * (NULL = the plan's own).  A workspace holds the receive buffers and the
- * dependency counters of one in-flight apply. */
+ * fused engine's barrier words of one in-flight apply. */
 int napspmv_apply_ex(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w,
                      int32_t reps, double scale, const napspmv_opts *opts, void *stream);
 
@@ -287,20 +289,20 @@ int napspmv_apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_
  * (a framework's memory pool) owns the device's free memory or because
  * cudaMalloc's implicit device synchronisation is not acceptable on their
  * path.  The plan must already exist (napspmv_plan allocates).
- *   - Receive buffers, the chain vector and dependency counters come from one
+ *   - Receive buffers, the chain vector and barrier words come from one
  *     fixed array of 2^20 doubles (8 MiB) that this library reserves on every
  *     device that loads it, until the process exits.  Plans needing more
  *     (see below) are rejected with NAPSPMV_ERR_UNSUPPORTED and a message
  *     giving both sizes.
  *   - Every call shares that array and it keeps the last call's contents;
- *     the counters are cleared by each call.  Calls that overlap on the GPU
+ *     the barrier words are cleared by each call.  Calls that overlap on the GPU
  *     (on different streams, or on different plans) race on it: order them.
  *   - The first call on a device looks the array's device address up (with
  *     that device current) and caches it for the life of the process: the
  *     cached address does not survive cudaDeviceReset on that device.
- *   - Scratch needed: counters + b_{l->l} + b_{l->nl} + 2 g_send + b_{nl->l}
+ *   - Scratch needed: 2 barrier words + b_{l->l} + b_{l->nl} + 2 g_send + b_{nl->l}
  *     values, plus N for the chain vector when reps > 1.
- *   - Uses the fused engine with the plan's current work items and FP64
+ *   - Uses the fused engine with the plan's default options and FP64
  *     values; device-side timeouts are reported by napspmv_status(P). */
 int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double *w, int32_t reps,
                           double scale, void *stream);

@@ -638,18 +638,6 @@ __device__ __forceinline__ bool staged_tile(const Item &it, int cap)
     return it.kind == kSpmv && it.k1 - it.k0 <= cap;
 }
 
-// The dependency counters of every job of a batched launch zeroed in one
-// launch (one block per job) instead of one memset per job.
-struct CtrZero {
-    unsigned long long *p[64];
-    int32_t n[64];
-};
-__global__ void __launch_bounds__(NT) k_zero_ctrs(const __grid_constant__ CtrZero Z)
-{
-    unsigned long long *p = Z.p[blockIdx.x];
-    for (int k = threadIdx.x; k < Z.n[blockIdx.x]; k += NT) p[k] = 0ull;
-}
-
 // --------------------------------------------------------- phased engine
 template <class T>
 __global__ void __launch_bounds__(NT)
@@ -1202,13 +1190,12 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? (U >= 8 ? 4 : 6) : 1)
 // part (the overlap Algorithm NAPSpMV allows) was measured slower on GB300:
 // the remote part's continuation of every row costs more than the local part
 // hides (3D 7-point 128^3: 152 against ~100 us per apply).  Within a level the
-// units of all jobs (message chunks of kFusedChunk elements, groups of
+// units of all jobs (message chunks of `chunk` elements, groups of
 // kSellGroup sliced-row chunks, groups of 8 long rows) are dealt to the CTAs
 // round robin: no ticket counter, no per-item dependency check, one barrier
 // per level.  Every CTA of the
 // cooperative launch is resident, so the barrier cannot wait on a CTA that
 // never runs; its wait is bounded all the same.
-constexpr int kFusedChunk = NT * 8;
 constexpr int kLevels = 4;
 // Elements per thread per pass in the message levels, and sliced-row entries
 // per step in level 3, whatever the row lengths.  With these the kernel fits
@@ -1235,6 +1222,7 @@ struct FJob {
     const double *v;
     double *w;
     int32_t nmsg[kLevels];      // message units per level
+    int32_t ch;                 // elements per message unit (option chunk)
     int32_t nunits[kLevels];    // all units per level
 };
 
@@ -1352,25 +1340,25 @@ __device__ __forceinline__ void fused_unit(const FJob &J, int lvl, int u, const 
     const int warp = tid >> 5, lane = tid & 31;
     const uint64_t pol = policy_evict_first();
     if (u < J.nmsg[lvl]) {
-        const int b = u * kFusedChunk;
+        const int b = u * J.ch;
         switch (lvl) {
         case 0: {
-            const int nu0 = (J.n0 + kFusedChunk - 1) / kFusedChunk;
+            const int nu0 = (J.n0 + J.ch - 1) / J.ch;
             if (u < nu0) {
-                step_gather<true, kFusedU>(J.bll, x, J.src0, b, min(J.n0, b + kFusedChunk), tid);
+                step_gather<true, kFusedU>(J.bll, x, J.src0, b, min(J.n0, b + J.ch), tid);
             } else {
-                const int b1 = (u - nu0) * kFusedChunk;
+                const int b1 = (u - nu0) * J.ch;
                 step_gather<true, kFusedU>(J.composed ? J.bnl : J.lbuf, x, J.src1, b1,
-                                     min(J.n1, b1 + kFusedChunk), tid);
+                                     min(J.n1, b1 + J.ch), tid);
             }
             break;
         }
         case 1:
             step_pack_transfer(J.gsend, J.grecv, x, J.lbuf, J.pack_src, J.xfer_dst, b,
-                               min(J.n_gs, b + kFusedChunk), tid);
+                               min(J.n_gs, b + J.ch), tid);
             break;
         default:
-            step_gather<true, kFusedU>(J.bnl, J.grecv, J.unp_src, b, min(J.n_bnl, b + kFusedChunk), tid);
+            step_gather<true, kFusedU>(J.bnl, J.grecv, J.unp_src, b, min(J.n_bnl, b + J.ch), tid);
             break;
         }
         return;
@@ -1460,56 +1448,18 @@ static size_t smem_bytes(int32_t tile_nnz, int32_t tile_rows, int32_t ns = 2, in
     return (size_t)tile_smem_bytes(tile_nnz, tile_rows, ns, vb);
 }
 
-int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t tile_nnz)
+int build_items(napspmv_plan_t *P, int32_t tile_rows, int32_t tile_nnz)
 {
-    if (chunk < 32 || tile_rows < 1 || tile_nnz < 32 ||
-        smem_bytes(tile_nnz, tile_rows) > 200 * 1024) {
-        set_error(NAPSPMV_ERR_ARG, "need chunk >= 32, tile_rows >= 1, tile_nnz >= 32 and "
-                                   "two tile stages (12 B per entry, 4 B per row) within 200 KiB");
+    if (tile_rows < 1 || tile_nnz < 32 || smem_bytes(tile_nnz, tile_rows) > 200 * 1024) {
+        set_error(NAPSPMV_ERR_ARG, "need tile_rows >= 1, tile_nnz >= 32 and two tile stages "
+                                   "(12 B per entry, 4 B per row) within 200 KiB");
         return NAPSPMV_ERR_ARG;
     }
     ItemSet &S = P->items;
-    if (S.d_items && S.chunk == chunk && S.tile_rows == tile_rows && S.tile_nnz == tile_nnz)
-        return NAPSPMV_OK;
+    if (S.d_items && S.tile_rows == tile_rows && S.tile_nnz == tile_nnz) return NAPSPMV_OK;
     const int nn = P->nn;
+    // CTA tiles of the whole matrix, cut within each node's rows
     std::vector<Item> items;
-    std::vector<uint64_t> cnt((size_t)kNumCounters * nn, 0);
-    auto add = [&](int kind, int node, int64_t b, int64_t e, int msg, int counter) {
-        Item it{};
-        it.kind = kind;
-        it.node = node;
-        it.b = (int32_t)b;
-        it.e = (int32_t)e;
-        it.msg = msg;
-        items.push_back(it);
-        cnt[(size_t)counter * nn + node]++;
-    };
-    for (int x = 0; x < nn; x++)
-        for (int64_t b = P->node_bll[x]; b < P->node_bll[x + 1]; b += chunk)
-            add(kGatherJ2, x, b, std::min<int64_t>(b + chunk, P->node_bll[x + 1]), 0, kC1);
-    for (int x = 0; x < nn; x++)
-        for (int64_t b = P->node_lbuf[x]; b < P->node_lbuf[x + 1]; b += chunk)
-            add(kGatherJ0, x, b, std::min<int64_t>(b + chunk, P->node_lbuf[x + 1]), 0, kC1);
-    int32_t lvl[6] = {0};
-    lvl[1] = (int32_t)items.size();
-    for (int x = 0; x < nn; x++)
-        for (int64_t b = P->node_gs[x]; b < P->node_gs[x + 1]; b += chunk)
-            add(kPack, x, b, std::min<int64_t>(b + chunk, P->node_gs[x + 1]), 0, kC2);
-    lvl[2] = (int32_t)items.size();
-    const std::vector<int64_t> &off = P->gs_msg_off;
-    for (int x = 0; x < nn; x++)
-        for (int64_t b = P->node_gs[x]; b < P->node_gs[x + 1]; b += chunk) {
-            int m = (int)(std::upper_bound(off.begin(), off.end(), b) - off.begin()) - 1;
-            add(kTransfer, x, b, std::min<int64_t>(b + chunk, P->node_gs[x + 1]), m, kC3);
-        }
-    for (size_t m = 0; m + 1 < off.size(); m++)
-        cnt[(size_t)kArr * nn + P->gs_msg_dstnode[m]] += (uint64_t)(off[m + 1] - off[m]);
-    lvl[3] = (int32_t)items.size();
-    for (int x = 0; x < nn; x++)
-        for (int64_t b = P->node_bnl[x]; b < P->node_bnl[x + 1]; b += chunk)
-            add(kUnpack, x, b, std::min<int64_t>(b + chunk, P->node_bnl[x + 1]), 0, kC4);
-    const int32_t spmv_first = (int32_t)items.size();
-    lvl[4] = spmv_first;
     const std::vector<int32_t> &rp = P->h_rowptr;
     for (int x = 0; x < nn; x++) {
         int64_t r = P->node_rows[x];
@@ -1518,9 +1468,14 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
             int64_t e = r;
             while (e < end && e - r < tile_rows && rp[e + 1] - rp[r] <= tile_nnz) e++;
             if (e == r) e = r + 1;  // one row longer than the capacity
-            add(kSpmv, x, r, e, 0, kC5);
-            items.back().k0 = rp[r];
-            items.back().k1 = rp[e];
+            Item it{};
+            it.kind = kSpmv;
+            it.node = x;
+            it.b = (int32_t)r;
+            it.e = (int32_t)e;
+            it.k0 = rp[r];
+            it.k1 = rp[e];
+            items.push_back(it);
             r = e;
         }
     }
@@ -1592,9 +1547,8 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
         cap = std::min(tnnz, (cap + 15) & ~15);
     };
     {
-        const std::vector<Item> whole(items.begin() + spmv_first, items.end());
         const int32_t wn = std::max(32, tile_nnz / 8);
-        fit(whole, tile_nnz, S.fit_nnz[0], S.fit_rows[0]);
+        fit(items, tile_nnz, S.fit_nnz[0], S.fit_rows[0]);
         fit(tl, tile_nnz, S.fit_nnz[1], S.fit_rows[1]);
         fit(tr, tile_nnz, S.fit_nnz[2], S.fit_rows[2]);
         fit(trh, tile_nnz, S.fit_nnz[6], S.fit_rows[6]);
@@ -1630,28 +1584,24 @@ int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t til
     S.n_tilesR = (int32_t)tr.size();
 
     Item *d_items = nullptr;
-    uint64_t *d_cnt = nullptr;
-    NAP_CUDA(cudaMalloc(&d_items, sizeof(Item) * items.size()));
-    NAP_CUDA(cudaMalloc(&d_cnt, sizeof(uint64_t) * cnt.size()));
-    NAP_CUDA(cudaMemcpy(d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice));
-    NAP_CUDA(cudaMemcpy(d_cnt, cnt.data(), sizeof(uint64_t) * cnt.size(), cudaMemcpyHostToDevice));
+    if (!items.empty()) {
+        NAP_CUDA(cudaMalloc(&d_items, sizeof(Item) * items.size()));
+        NAP_CUDA(cudaMemcpy(d_items, items.data(), sizeof(Item) * items.size(),
+                            cudaMemcpyHostToDevice));
+    }
     if (S.d_items) cudaFree(S.d_items);
-    if (S.d_cnt) cudaFree(S.d_cnt);
-    for (auto &g : P->graphs) cudaGraphExecDestroy(g.exec);  // they captured the old items
+    for (auto &g : P->graphs) cudaGraphExecDestroy(g.exec);  // they captured the old tiles
     P->graphs.clear();
     S.d_items = d_items;
-    S.d_cnt = d_cnt;
     S.n_items = (int32_t)items.size();
-    S.spmv_first = spmv_first;
-    lvl[5] = (int32_t)items.size();
-    std::copy(lvl, lvl + 6, S.lvl);
-    S.chunk = chunk;
     S.tile_rows = tile_rows;
     S.tile_nnz = tile_nnz;
     return NAPSPMV_OK;
 }
 
-static size_t ctr_count(const napspmv_plan_t *P) { return 2 + (size_t)kNumCounters * P->nn; }
+// Counter words of a workspace: the fused engine's grid barrier (arrival count
+// and generation).
+static size_t ctr_count(const napspmv_plan_t *) { return 2; }
 
 int ws_alloc(napspmv_plan_t *P, napspmv_ws_t *ws)
 {
@@ -1726,7 +1676,7 @@ static SellView sell_view(const napspmv_plan_t *P, int part, bool f32)
 static int32_t cdiv(int64_t a, int64_t b) { return (int32_t)((a + b - 1) / b); }
 
 static FJob make_job(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, double *w, int reps,
-                     double scale, bool f32)
+                     double scale, bool f32, int32_t chunk)
 {
     FJob J{};
     J.F = sell_view(P, 0, f32);
@@ -1758,10 +1708,11 @@ static FJob make_job(napspmv_plan_t *P, napspmv_ws_t *ws, const double *v, doubl
     J.w = w;
     // units of every level: message chunks (levels 0-2), the sliced rows'
     // chunk groups and long rows (level 3)
-    J.nmsg[0] = cdiv(J.n0, kFusedChunk) + cdiv(J.n1, kFusedChunk);
+    J.ch = chunk;
+    J.nmsg[0] = cdiv(J.n0, J.ch) + cdiv(J.n1, J.ch);
     if (!J.composed) {
-        J.nmsg[1] = cdiv(J.n_gs, kFusedChunk);
-        J.nmsg[2] = cdiv(J.n_bnl, kFusedChunk);
+        J.nmsg[1] = cdiv(J.n_gs, J.ch);
+        J.nmsg[2] = cdiv(J.n_bnl, J.ch);
     }
     for (int l = 0; l < 3; l++) J.nunits[l] = J.nmsg[l];
     J.nunits[3] = cdiv(J.F.nch, kSellGroup) + cdiv(J.F.n_long, WPB);
@@ -1783,7 +1734,7 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
     int32_t acc[kLevels] = {};
     for (int i = 0; i < count; i++) {
         napspmv_ws_t *wi = ws && ws[i] ? ws[i] : plans[i]->ws;
-        prm.jobs[i] = make_job(plans[i], wi, v[i], w[i], reps[i], scale ? scale[i] : 1.0, f32);
+        prm.jobs[i] = make_job(plans[i], wi, v[i], w[i], reps[i], scale ? scale[i] : 1.0, f32, o.chunk);
         prm.kmax = std::max(prm.kmax, reps[i]);
         for (int l = 0; l < kLevels; l++) {
             prm.off[l][i] = acc[l];
@@ -2001,8 +1952,8 @@ static int spmv_launch(const napspmv_plan_t *P, const napspmv_opts &o, int mode,
     } else {
         L.A = Csr3{P->d_rowptr, P->d_colenc, P->d_val, f32 ? P->d_val32 : nullptr};
         L.fn = f32 ? pick_spmv<true, kFull>(o.vec, warp) : pick_spmv<false, kFull>(o.vec, warp);
-        L.tiles = warp ? S.d_wt : S.d_items + S.spmv_first;
-        L.n = warp ? S.n_wt : S.n_items - S.spmv_first;
+        L.tiles = warp ? S.d_wt : S.d_items;
+        L.n = warp ? S.n_wt : S.n_items;
     }
     const void *kf = L.hfn ? (const void *)L.hfn : (const void *)L.fn;
     if (L.sm > 48 * 1024)
@@ -2323,6 +2274,10 @@ int check_opts(const napspmv_plan_t *P, const napspmv_opts &o)
         set_error(NAPSPMV_ERR_ARG, "timeout_ms must be >= 1");
         return NAPSPMV_ERR_ARG;
     }
+    if (o.chunk < 32 || o.chunk > (1 << 24)) {
+        set_error(NAPSPMV_ERR_ARG, "chunk must be 32 .. 2^24 elements");
+        return NAPSPMV_ERR_ARG;
+    }
     if (o.halo != NAPSPMV_HALO_ON && o.halo != NAPSPMV_HALO_OFF) {
         set_error(NAPSPMV_ERR_ARG, "halo must be NAPSPMV_HALO_ON or _OFF");
         return NAPSPMV_ERR_ARG;
@@ -2394,7 +2349,7 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
         // validate them for that engine
         if (count > 1) oi[i].engine = NAPSPMV_ENGINE_FUSED;
         if ((rc = check_opts(P, oi[i]))) break;
-        if ((rc = build_items(P, oi[i].chunk, oi[i].tile_rows, oi[i].tile_nnz))) break;
+        if ((rc = build_items(P, oi[i].tile_rows, oi[i].tile_nnz))) break;
         for (int q = 0; q < i; q++) {
             napspmv_ws_t *a = ws && ws[i] ? ws[i] : P->ws;
             napspmv_ws_t *b = ws && ws[q] ? ws[q] : plans[q]->ws;
@@ -2536,11 +2491,12 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
     q += P->n_bnl;
     view.xtmp = reps > 1 ? q : nullptr;
     view.err = P->ws->err;
-    // the plan's current work items and matching options: nothing is rebuilt
+    // the plan's default options on the fused engine, FP64; the tile shape is
+    // the one the plan's row tiles have, so that nothing is rebuilt (the fused
+    // engine sums rows from the sliced-row copy)
     napspmv_opts o = P->defaults;
     o.engine = NAPSPMV_ENGINE_FUSED;
     o.precision = NAPSPMV_PREC_F64;
-    o.chunk = P->items.chunk;
     o.tile_rows = P->items.tile_rows;
     o.tile_nnz = P->items.tile_nnz;
     o.debug_stall = 0;
@@ -2578,7 +2534,7 @@ extern "C" int napspmv_spmv_step(napspmv_plan_t *P, napspmv_ws_t *ws, const doub
     int cur = 0;
     NAP_CUDA(cudaGetDevice(&cur));
     if (cur != P->device) NAP_CUDA(cudaSetDevice(P->device));
-    if ((rc = build_items(P, o.chunk, o.tile_rows, o.tile_nnz))) return rc;
+    if ((rc = build_items(P, o.tile_rows, o.tile_nnz))) return rc;
     const bool f32 = o.precision == NAPSPMV_PREC_F32;
     // launched as the phased engine launches its SpMV pass
     const bool pdl = o.engine == NAPSPMV_ENGINE_PHASED;

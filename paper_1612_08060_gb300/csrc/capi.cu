@@ -216,7 +216,7 @@ int napspmv_set_default_opts(napspmv_plan_t *P, const napspmv_opts *opts)
     int cur = 0;
     NAP_CUDA(cudaGetDevice(&cur));
     if (cur != P->device) NAP_CUDA(cudaSetDevice(P->device));
-    int rc = build_items(P, o.chunk, o.tile_rows, o.tile_nnz);
+    int rc = build_items(P, o.tile_rows, o.tile_nnz);
     if (cur != P->device) cudaSetDevice(cur);
     if (rc) return rc;
     P->defaults = o;

@@ -37,34 +37,23 @@ constexpr uint32_t kIndexMask = (1u << 30) - 1;
 // otherwise v.
 constexpr uint32_t kFromLbuf = 0x80000000u;
 
-// --------------------------------------------------------- fused work items
+// ------------------------------------------------- row tiles (CTA and warp)
 enum ItemKind : int32_t {
-    kGatherJ2 = 0,  // b_{l->l}[k]  = v[bll_j[k]]          (on_node -> on_node)
-    kGatherJ0 = 1,  // b_{l->nl}[k] = v[lbuf_j[k]]         (on_node -> off_node)
-    kPack = 2,      // g_send[k] = v or b_{l->nl} (pack_src[k])
-    kTransfer = 3,  // g_recv[xfer_dst[k]] = g_send[k]     (inter-node)
-    kUnpack = 4,    // b_{nl->l}[k] = g_recv[unp_src[k]]   (off_node -> on_node)
-    kSpmv = 5,      // rows [b, e) of the three-block SpMV
+    kSpmv = 5,  // rows [b, e) of the three-block SpMV
 };
-// Dependency counters per node, in this order, then the arrival counter.
-enum Counter : int32_t { kC1 = 0, kC2 = 1, kC3 = 2, kC4 = 3, kC5 = 4, kArr = 5, kNumCounters = 6 };
 
 struct Item {
     int32_t kind;
-    int32_t node;  // node whose data the item touches (sender node for kTransfer)
-    int32_t b, e;  // element (or row) range
-    int32_t msg;   // kTransfer: first g_send message overlapping [b, e)
-    int32_t k0, k1;  // kSpmv: stored-entry range [row_ptr[b], row_ptr[e])
+    int32_t node;    // node of the rows
+    int32_t b, e;    // row range
+    int32_t msg;     // remote tiles cut at process bounds: the process
+    int32_t k0, k1;  // stored-entry range [row_ptr[b], row_ptr[e])
     int32_t pad;
 };
 
 struct ItemSet {
-    int32_t chunk = 0, tile_rows = 0, tile_nnz = 0;
-    int32_t n_items = 0;
-    int32_t spmv_first = 0;  // items [spmv_first, n_items) are the row tiles
-    // items [lvl[L], lvl[L+1]) are level L of the dataflow: gathers, packs,
-    // transfers, unpacks, row tiles
-    int32_t lvl[6] = {};
+    int32_t tile_rows = 0, tile_nnz = 0;
+    int32_t n_items = 0;  // CTA tiles of the whole matrix (d_items)
     Item *d_tilesL = nullptr, *d_tilesR = nullptr;  // tiles of the split parts
     int32_t n_tilesL = 0, n_tilesR = 0;
     // remote tiles cut at process boundaries (Item::msg = process), for the
@@ -80,8 +69,6 @@ struct ItemSet {
     // cut per process: a stage is sized to what its list needs, not to tile_nnz
     int32_t fit_nnz[7] = {}, fit_rows[7] = {};
     Item *d_items = nullptr;
-    // per-apply increments of every counter, [kNumCounters][nn]
-    uint64_t *d_cnt = nullptr;
 };
 
 // --------------------------------------------------------------- plan lists
@@ -131,7 +118,7 @@ struct napspmv_ws_s {
     float *x32[2] = {nullptr, nullptr};
     int buf_f32 = 0;
     double *hv = nullptr, *hw = nullptr;  // staging of napspmv_apply_host
-    unsigned long long *ctr = nullptr;  // ticket + kNumCounters * nn
+    unsigned long long *ctr = nullptr;  // the fused engine's grid barrier: arrivals, generation
     int *err = nullptr;                 // sticky device status
     bool owned_by_plan = false;
 };
@@ -175,13 +162,9 @@ struct napspmv_plan_s {
     int32_t *d_unp_src = nullptr;    // [n_bnl]
     // BLL / LBUF list idx arrays double as the J2 / J0 gather sources.
 
-    // per-node ranges (host) used to cut work items
-    std::vector<int64_t> node_bll, node_lbuf, node_gs, node_bnl, node_rows;  // [nn+1]
+    // first row of every node (host), where the CTA row tiles are cut
+    std::vector<int64_t> node_rows;  // [nn+1]
     std::vector<int32_t> h_rowptr;         // host copy of the row pointer, for tiling
-    std::vector<int64_t> gs_msg_off;       // [n_inter + 1] g_send offsets in INTER order
-    std::vector<int32_t> gs_msg_dstnode;   // [n_inter]
-    int32_t *d_gs_msg_off = nullptr;       // device copies
-    int32_t *d_gs_msg_dstnode = nullptr;
 
     // sliced-row copies of the whole matrix, its local part and its remote
     // part (index 0, 1, 2), for NAPSPMV_PIPELINE_SELL; built with the plan
@@ -203,7 +186,7 @@ struct napspmv_plan_s {
 };
 
 namespace nap {
-int build_items(napspmv_plan_t *P, int32_t chunk, int32_t tile_rows, int32_t tile_nnz);
+int build_items(napspmv_plan_t *P, int32_t tile_rows, int32_t tile_nnz);
 int ws_alloc(napspmv_plan_t *P, napspmv_ws_t *ws);
 void ws_free(napspmv_ws_t *ws);
 void plan_free(napspmv_plan_t *P);

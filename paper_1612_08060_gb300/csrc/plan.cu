@@ -996,13 +996,12 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
     // g_send in (src, dst) order: offsets, and per message (in that order) its
     // pair, first position in E(n,m), sender and g_recv offset
     std::vector<int64_t> gs_off(NM + 1, 0), msg_gr(NM), msg_lo(NM);
-    std::vector<int32_t> msg_pair(NM), msg_src(NM), msg_dstnode(NM);
+    std::vector<int32_t> msg_pair(NM), msg_src(NM);
     for (int64_t i = 0; i < NM; i++) {
         const Msg &mg = msgs[sorder[i]];
         gs_off[i + 1] = gs_off[i] + (mg.hi - mg.lo);
         msg_pair[i] = mg.pair;
         msg_src[i] = mg.src;
-        msg_dstnode[i] = ND.dst[mg.pair];
         msg_gr[i] = gr_off[sorder[i]];
         msg_lo[i] = mg.lo;
     }
@@ -1187,28 +1186,13 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
     }
     CK(cudaDeviceSynchronize());
 
-    // ---- per-node ranges for cutting work items
-    P->node_bll.assign(nn + 1, 0);
-    P->node_lbuf.assign(nn + 1, 0);
-    P->node_bnl.assign(nn + 1, 0);
+    // ---- first row of every node, where the CTA row tiles are cut
     P->node_rows.assign(nn + 1, 0);
-    P->node_gs.assign(nn + 1, 0);
     for (int32_t x = 0; x <= nn; x++) {
         int32_t r = std::min<int64_t>((int64_t)x * ppn, np);
-        P->node_bll[x] = bll_ptr[r];
-        P->node_lbuf[x] = lbuf_ptr[r];
-        P->node_bnl[x] = bnl_ptr[r];
         // strided: every node's rows interleave; the row tiles are cut over
-        // all rows as one range (only the phased engines run such plans)
+        // all rows as one range
         P->node_rows[x] = part.strided ? (x == 0 ? 0 : n) : part.start(r);
-    }
-    {
-        int64_t i = 0;
-        for (int32_t x = 0; x <= nn; x++) {
-            int64_t first_rank = (int64_t)x * ppn;
-            while (i < NM && msg_src[i] < first_rank) i++;
-            P->node_gs[x] = gs_off[i];
-        }
     }
     {
         std::vector<int64_t> h(n + 1);
@@ -1221,13 +1205,6 @@ void build(napspmv_plan_t *P, const napspmv_csr *A)
     build_sell(P, 1, P->h_rowptrL, P->d_rowptrL, P->d_colL, P->d_valL, P->d_val32L, part);
     build_sell(P, 2, P->h_rowptrR, P->d_rowptrR, P->d_colR, P->d_valR, P->d_val32R, part);
     CK(cudaDeviceSynchronize());
-
-    P->gs_msg_off = gs_off;
-    P->gs_msg_dstnode = msg_dstnode;
-    std::vector<int32_t> gs_off32(NM + 1);
-    for (int64_t i = 0; i <= NM; i++) gs_off32[i] = (int32_t)gs_off[i];
-    P->d_gs_msg_off = upload(gs_off32);
-    P->d_gs_msg_dstnode = upload(msg_dstnode);
 
     host_stats(P);
 }
@@ -1248,8 +1225,8 @@ void plan_free(napspmv_plan_t *P)
     for (auto &L : P->lists)
         if (L.d_idx) cudaFree(L.d_idx);
     void *ptrs[] = {P->d_split, P->d_rowptr, P->d_colenc, P->d_val, P->d_val32, P->d_pack_src,
-                    P->d_xfer_dst, P->d_unp_src, P->d_gs_msg_off, P->d_gs_msg_dstnode,
-                    P->items.d_items, P->items.d_cnt, P->items.d_tilesL, P->items.d_tilesR,
+                    P->d_xfer_dst, P->d_unp_src,
+                    P->items.d_items, P->items.d_tilesL, P->items.d_tilesR,
                     P->items.d_wt, P->items.d_wtL, P->items.d_wtR, P->items.d_tilesRH,
                     P->d_rowptrL, P->d_rowptrR, P->d_colL, P->d_colR, P->d_valL, P->d_valR,
                     P->d_val32L, P->d_val32R, P->d_bll_rank, P->d_bnl_rank};
@@ -1343,7 +1320,7 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         P->defaults.engine = engine;
         P->defaults.vec = vec;
         P->defaults.ctas_per_sm = ctas;
-        P->defaults.chunk = 4096;
+        P->defaults.chunk = 2048;
         P->defaults.tile_rows = rows;
         P->defaults.tile_nnz = cap;
         P->defaults.stages = 2;
@@ -1351,8 +1328,8 @@ int plan_create(const napspmv_csr *A, int32_t np, int32_t ppn, uint32_t flags,
         P->defaults.halo = NAPSPMV_HALO_ON;
         P->defaults.timeout_ms = 10000;
         P->defaults.debug_stall = 0;
-        rc = build_items(P, P->defaults.chunk, P->defaults.tile_rows, P->defaults.tile_nnz);
-        if (rc) throw NapError{rc, "work-item construction failed"};
+        rc = build_items(P, P->defaults.tile_rows, P->defaults.tile_nnz);
+        if (rc) throw NapError{rc, "row-tile construction failed"};
     } catch (const NapError &e) {
         plan_free(P);
         set_error(e.code, e.msg);

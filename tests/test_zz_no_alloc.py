@@ -25,15 +25,14 @@ SCRATCH_DOUBLES = 1 << 20
 def _scratch_need(plan, A, n_p, ppn, reps):
     """Doubles of the static array one call needs (as the header states)."""
     st = nap.napspmv_plan_stats(plan)
-    n_nodes = -(-n_p // ppn)
-    need = (2 + 6 * n_nodes + st["bll_total"] + st["lbuf_total"] + 2 * st["nap_inter_vals"] +
+    need = (2 + st["bll_total"] + st["lbuf_total"] + 2 * st["nap_inter_vals"] +
             st["bnl_total"])
     return need + (A.n if reps > 1 else 0)
 
 
 def _fused_opts_of_noalloc(plan, tile_rows=None, tile_nnz=None, chunk=None):
     """The options napspmv_apply_noalloc runs with: the plan's defaults on the
-    fused engine, FP64, and the tile shape of the plan's current work items."""
+    fused engine, FP64, and the tile shape of the plan's current row tiles."""
     o = nap.napspmv_get_default_opts(plan)
     o.engine = nap.ENGINE_FUSED
     o.precision = nap.PREC_F64
