@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 def test_tune_installs_and_caches(monkeypatch, tmp_path):
     monkeypatch.setattr(autotune, "CANDIDATES", {
         "engine": [nap.ENGINE_OVERLAP, nap.ENGINE_FUSED], "vec": [1, 2],
-        "tile_nnz": [1024, 1536], "tile_rows": [256, 512], "stages": [2], "chunk": [4096]})
+        "tile_nnz": [1024, 1536], "tile_rows": [256, 512], "stages": [2], "chunk": [2048]})
     monkeypatch.setattr(autotune, "_cache", {})
     A = I.poisson3d(32)
     plan = gpu_plan(A, 16, 4)
