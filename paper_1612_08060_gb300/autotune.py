@@ -4,7 +4,7 @@ Searches the engine (overlapped, phased, fused), lanes per row (``vec``), the
 SpMV tile shape (``tile_rows``, ``tile_nnz``: the entries one shared-memory
 stage holds), the pipeline depth (``stages``), CTA or warp tiles
 (``pipeline``), resident CTAs per SM (``ctas_per_sm``, 0 = occupancy maximum)
-and the gather chunk of the fused engine's message items (``chunk``) by
+and the elements per message unit of the fused engine (``chunk``) by
 coordinate descent: starting from the plan's defaults, each parameter in turn
 is set to each candidate while the others stay fixed, the fastest is kept, and
 the sweep repeats until nothing improves.  Each candidate is timed with CUDA
