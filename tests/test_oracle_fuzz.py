@@ -13,7 +13,8 @@ hyp = pytest.importorskip("hypothesis")
 st = pytest.importorskip("hypothesis.strategies")
 
 FLAGS = [0, O.MAP_TEXT, O.STRIDED, O.MAP_MAJORITY, O.STRIDED | O.MAP_TEXT,
-         O.STRIDED | O.MAP_MAJORITY]
+         O.STRIDED | O.MAP_MAJORITY, O.MAP_SPLIT, O.MAP_SPLIT | O.MAP_TEXT,
+         O.STRIDED | O.MAP_SPLIT]
 
 
 @st.composite
@@ -44,7 +45,8 @@ def test_oracle_agrees_with_set_definitions(prob):
     rows = [set(col[row_ptr[i]:row_ptr[i + 1]].tolist()) for i in range(n)]
     plan = O.OraclePlan(row_ptr, col, n_p, ppn, flags=flags)
     b = brute_plan(n, rows, n_p, ppn, map_text=bool(flags & O.MAP_TEXT),
-                   strided=bool(flags & O.STRIDED), majority=bool(flags & O.MAP_MAJORITY))
+                   strided=bool(flags & O.STRIDED), majority=bool(flags & O.MAP_MAJORITY),
+                   split=bool(flags & O.MAP_SPLIT))
     for name, kind in [("STD", O.STD), ("NODE", O.NODE), ("INTER", O.INTER), ("J0", O.J0),
                        ("J1", O.J1), ("J2", O.J2)]:
         assert plan.list_dict(kind) == b[name], name
