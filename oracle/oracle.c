@@ -300,6 +300,10 @@ int orc_plan_build(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t
     int rc = ORC_OK;
     *out = NULL;
     if (np < 1 || np > n || ppn < 1) return ORC_ERR_ARG;
+    /* unknown bits are refused, not ignored: a caller's flag from another
+     * numbering must not silently select the default mapping */
+    if (flags & ~(int64_t)(ORC_MAP_TEXT | ORC_STRIDED | ORC_MAP_MAJORITY | ORC_MAP_SPLIT))
+        return ORC_ERR_ARG;
     if ((flags & ORC_MAP_MAJORITY) && (flags & (ORC_MAP_TEXT | ORC_MAP_SPLIT))) return ORC_ERR_ARG;
     rc = check_csr(n, nnz, row_ptr, col);
     if (rc) return rc;

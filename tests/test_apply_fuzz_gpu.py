@@ -1,6 +1,6 @@
 """Seeded random draws of matrix and launch options (engine, precision, lanes
 per row, CTA, warp or sliced-row tiles, tile shape, staged receive buffers, chain length,
-partition flags): every apply matches the oracle within the FP64 bound, or the
+partition and mapping flags): every apply matches the oracle within the FP64 bound, or the
 oracle's FP32-value product within 1e-13 in FP32 mode."""
 import numpy as np
 import pytest
@@ -34,10 +34,9 @@ def _draws(count=60, seed=4242):
         A = _matrix(rng)
         n_p = int(rng.integers(1, min(A.n, 300) + 1))
         ppn = int(rng.integers(1, 17))
-        flags = int(rng.choice([0, 0, nap.MAP_TEXT, nap.MAP_MAJORITY, nap.PARTITION_STRIDED]))
+        flags = int(rng.choice([0, 0, nap.MAP_TEXT, nap.MAP_MAJORITY, nap.PARTITION_STRIDED,
+                                nap.MAP_SPLIT]))
         eng = int(rng.choice(ENGINES))
-        if flags & nap.PARTITION_STRIDED and eng == nap.ENGINE_FUSED:
-            eng = nap.ENGINE_OVERLAP
         prec = int(rng.choice([nap.PREC_F64, nap.PREC_F32]))
         opts = dict(engine=eng, precision=prec, vec=int(rng.choice([1, 2, 4, 8, 16, 32])),
                     pipeline=int(rng.choice([nap.PIPELINE_CTA, nap.PIPELINE_WARP, nap.PIPELINE_SELL])),

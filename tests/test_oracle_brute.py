@@ -283,3 +283,11 @@ def test_split_with_majority_rejected():
     A = random_pattern(12, 0.3, 1)
     with pytest.raises(ValueError):
         O.OraclePlan(A.row_ptr, A.col, 4, 2, flags=O.MAP_MAJORITY | O.MAP_SPLIT)
+
+
+def test_unknown_flag_bits_rejected():
+    """A flag bit the oracle does not define is refused, not ignored."""
+    A = random_pattern(12, 0.3, 1)
+    for bad in (1, 32, 64, 1 << 20):
+        with pytest.raises(Exception):
+            O.OraclePlan(A.row_ptr, A.col, 4, 2, flags=bad)

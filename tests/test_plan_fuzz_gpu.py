@@ -13,7 +13,17 @@ from paper_1612_08060_gb300 import napspmv as nap
 pytestmark = pytest.mark.gpu
 
 FLAGS = [0, nap.MAP_TEXT, nap.PARTITION_STRIDED, nap.MAP_MAJORITY,
-         nap.PARTITION_STRIDED | nap.MAP_TEXT, nap.PARTITION_STRIDED | nap.MAP_MAJORITY]
+         nap.PARTITION_STRIDED | nap.MAP_TEXT, nap.PARTITION_STRIDED | nap.MAP_MAJORITY,
+         nap.MAP_SPLIT, nap.MAP_SPLIT | nap.MAP_TEXT, nap.PARTITION_STRIDED | nap.MAP_SPLIT]
+
+
+# the library's and the oracle's flag bits are numbered independently
+_TO_ORACLE = {nap.MAP_TEXT: O.MAP_TEXT, nap.PARTITION_STRIDED: O.STRIDED,
+              nap.MAP_MAJORITY: O.MAP_MAJORITY, nap.MAP_SPLIT: O.MAP_SPLIT}
+
+
+def _oracle_flags(flags):
+    return sum(o for g, o in _TO_ORACLE.items() if flags & g)
 
 
 def _draws(count=80, seed=2024):
@@ -29,7 +39,7 @@ def _draws(count=80, seed=2024):
 def test_random_draw(q, n, dens, diag, n_p, ppn, flags, seed):
     A = I.random_pattern(n, dens, seed, diag=diag)
     gp = nap.napspmv_plan(A.row_ptr, A.col, A.val, n_p, ppn, flags | nap.F32_VALUES)
-    op = O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=flags)
+    op = O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=_oracle_flags(flags))
     assert_plans_equal(gp, op)
     v = I.vector(n, seed + 1)
     w = torch.empty(n, dtype=torch.float64, device="cuda")
