@@ -12,31 +12,29 @@
 //            off_node from b_{nl->l} (the three local_spmv of the algorithm as
 //            one pass over each row, blocks in that order)
 //
-// Row tiles (all engines): one thread copies a tile's row-pointer, column and
-// value slices into a shared-memory stage with bulk asynchronous copies counted
-// on an mbarrier; the next tile's copy overlaps the current tile.  Each row is
-// then summed from shared memory by one lane (vec lanes for long rows) with x
-// and the receive buffers gathered from L2/HBM: one DFMA per stored entry (FP64
+// SpMV pipelines: sliced rows (rows sorted by length, 32 to a chunk,
+// column-major, one lane per row, no shared-memory stage; the default for rows
+// of more than 12 entries and the fused engine's), and CTA or warp row tiles.
+// A row tile: one thread copies the tile's row-pointer, column and value slices
+// into a shared-memory stage with bulk asynchronous copies counted on an
+// mbarrier; the next tile's copy overlaps the current tile.  Each row is then
+// summed from shared memory by one lane (vec lanes for long rows) with x and
+// the receive buffers gathered from L2/HBM: one DFMA per stored entry (FP64
 // issue, not only HBM, bounds the SpMV on GB300).  Stages are sized to each
-// tile list's largest tile; tiles are handed to CTAs in contiguous runs; a CTA
-// pipeline and a warp pipeline (each warp its own stages) are provided.
+// tile list's largest tile; tiles are handed to CTAs in contiguous runs.
 //
 // Engines:
-//   overlapped (default)  the matrix split into its on_process part (local,
-//       needs no message) and its remote part; the local pass runs on a second
-//       stream while the message steps run, the remote pass continues each
-//       row's FMA chain from the local partial.  Where remote rows are
-//       gather-heavy, the remote pass stages each process's receive buffers in
-//       shared memory.
-//   phased   one kernel per phase per apply with the single-pass SpMV.
-//   fused    one persistent launch for all phases and applies: CTAs take work
-//       items (chunks of a node's gather ranges, tiles of a node's rows) from a
-//       global ticket counter in topological order; before an item runs,
-//       thread 0 waits (bounded, with a device error flag on timeout) on
-//       per-node counters of the items it depends on.  Tickets are handed out
-//       in order and an item only waits on earlier tickets, so progress never
-//       depends on how many CTAs are resident.  It also runs batches of
-//       independent applies in one launch.
+//   overlapped (default for rows of at most 12 entries)  the matrix split into
+//       its on_process part (local, needs no message) and its remote part; the
+//       local pass runs on a second stream while the message steps run, the
+//       remote pass continues each row's FMA chain from the local partial.
+//       Where remote rows are gather-heavy, the remote pass stages each
+//       process's receive buffers in shared memory.
+//   phased (default for longer rows)  one kernel per phase per apply with the
+//       single-pass SpMV.
+//   fused    one persistent, cooperative launch for all phases and applies of
+//       one or more jobs, in levels separated by bounded grid barriers (see
+//       k_fused).  It also runs batches of independent applies in one launch.
 // The phased engines capture chained applies into CUDA graphs and launch
 // dependent kernels programmatically (resident while the predecessor drains).
 // With one lane per row every engine gives the same bits.
@@ -154,9 +152,9 @@ __device__ __forceinline__ long long globaltimer()
 
 // Vector loads.  Fused engine: data written earlier in the same launch by
 // other CTAs is read with plain (weak, L1-cacheable) loads; they are ordered
-// after the producers' writes by thread 0's acquire fence on the dependency
-// counters followed by the CTA barrier.  Phased engine: every vector is
-// read-only for the kernel's lifetime and may use the read-only path.
+// after the producers' writes by thread 0's acquire fence in the grid barrier
+// followed by the CTA barrier.  Phased engine: every vector is read-only for
+// the kernel's lifetime and may use the read-only path.
 template <bool INKERNEL>
 __device__ __forceinline__ double ldx(const double *p)
 {
@@ -1743,7 +1741,7 @@ static int launch_fused(int count, napspmv_plan_t *const *plans, napspmv_ws_t *c
         wi->buf_f32 = 0;  // this engine's receive buffers hold FP64 values in both modes
     }
     for (int l = 0; l < kLevels; l++) prm.off[l][count] = acc[l];
-    // barrier words and the test hook's counter: the first job's counters
+    // barrier words and the test hook's counter: the first job's workspace words
     napspmv_ws_t *w0 = ws && ws[0] ? ws[0] : plans[0]->ws;
     prm.bar = reinterpret_cast<unsigned int *>(w0->ctr);
     prm.stallctr = w0->ctr + 1;
@@ -2326,7 +2324,7 @@ int apply_batch(int32_t count, napspmv_plan_t *const *plans, napspmv_ws_t *const
         return NAPSPMV_ERR_ARG;
     }
     // every entry resolves the unset fields against its own plan's defaults,
-    // so that it runs with the work items its plan already holds
+    // so that it runs with the row tiles its plan already holds
     napspmv_opts oi[64];
     int cur = 0;
     NAP_CUDA(cudaGetDevice(&cur));
@@ -2417,7 +2415,7 @@ extern "C" int64_t napspmv_launch_count(void) { return nap::g_launches; }
 // memory pool that holds the free memory), or they run on a latency-critical
 // path where cudaMalloc's implicit device synchronisation would stall their
 // pipeline.  napspmv_apply_noalloc serves them: it runs the fused apply with
-// its receive buffers, chain vector and dependency counters carved out of the
+// its receive buffers, chain vector and barrier words carved out of the
 // fixed array below instead of a workspace.  The array is reserved on every
 // device that loads this library, until the process exits.
 namespace nap {
@@ -2435,7 +2433,7 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
         set_error(NAPSPMV_ERR_ARG, "NULL plan or vector, reps < 1, or w == v");
         return NAPSPMV_ERR_ARG;
     }
-    // doubles of scratch: counters (as 8-byte words), b_{l->l}, b_{l->nl},
+    // doubles of scratch: the barrier words (8-byte), b_{l->l}, b_{l->nl},
     // g_send, g_recv, b_{nl->l}, and the chain vector when reps > 1 (a single
     // apply writes w directly)
     const int64_t words = (int64_t)ctr_count(P);
@@ -2508,7 +2506,7 @@ extern "C" int napspmv_apply_noalloc(napspmv_plan_t *P, const double *v, double 
     napspmv_plan_t *pl[1] = {P};
     const double *vl[1] = {v};
     double *wl[1] = {w};
-    // launch_fused zeroes the counters (the array keeps the last call's contents)
+    // launch_fused zeroes the barrier words (the array keeps the last call's contents)
     int rc = launch_fused<1>(1, pl, wsl, vl, wl, &reps, &scale, o, (cudaStream_t)stream);
     view.bll = view.lbuf = view.gsend = view.grecv = view.bnl = view.xtmp = nullptr;
     view.ctr = nullptr;
