@@ -25,6 +25,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -145,6 +146,64 @@ def ncu_record(workload, what):
     if d.get("kernel_hash") != kernel_hash():
         return None
     return d.get("records", {}).get(f"{workload}|{what}")
+
+
+# kernels of an apply and of the SpMV step, as ncu names them
+_APPLY_KERNELS = re.compile(r"k_gather2|k_pack|k_transfer|k_unpack|k_spmv|k_to_f32|k_fused")
+
+
+def ncu_launches(csv_path):
+    """Per-launch metrics of an `ncu --csv` log: [(kernel name, {metric: value})]
+    in launch order."""
+    import csv
+    lines = [ln for ln in open(csv_path) if not ln.startswith("==")]
+    rows = list(csv.reader(lines))
+    hdr = rows[0]
+    i_id, i_name = hdr.index("ID"), hdr.index("Kernel Name")
+    i_met, i_val = hdr.index("Metric Name"), hdr.index("Metric Value")
+    per = {}
+    for r in rows[1:]:
+        if len(r) <= i_val:
+            continue
+        per.setdefault((int(r[i_id]), r[i_name]), {})[r[i_met]] = float(r[i_val].replace(",", ""))
+    return [(name, m) for (_, name), m in sorted(per.items())]
+
+
+def ncu_summary(csv_path, nsteps=2, per_step=1):
+    """DRAM record of one `--profile-spmv nsteps` run: the kernels after the
+    last plan-build kernel are one apply, then nsteps SpMV steps of per_step
+    launches each (FP32 values: the FP32 copy of x, then the SpMV)."""
+    items = []
+    for name, m in ncu_launches(csv_path):
+        short = name.split("(")[0].replace("void ", "").replace("nap::", "")
+        items.append((short.replace("<unnamed>::", ""), m))
+    first = max(j for j, (n, _) in enumerate(items) if not _APPLY_KERNELS.search(n))
+    rest = items[first + 1:]
+    steps, apply_ = rest[len(rest) - nsteps * per_step:], rest[:len(rest) - nsteps * per_step]
+    b = lambda m: m.get("dram__bytes_read.sum", 0) + m.get("dram__bytes_write.sum", 0)  # noqa: E731
+    t = lambda m: m.get("gpu__time_duration.sum", 0) / 1e3  # noqa: E731
+    return {
+        "apply_bytes": sum(b(m) for _, m in apply_),
+        "apply_us_serialised": round(sum(t(m) for _, m in apply_), 2),
+        "per_kernel": [{"kernel": n, "dram_read": m.get("dram__bytes_read.sum"),
+                        "dram_write": m.get("dram__bytes_write.sum"), "us": round(t(m), 2)}
+                       for n, m in apply_],
+        "spmv_step_bytes": sum(b(m) for _, m in steps) / nsteps,
+        "spmv_step_kernels": [n for n, _ in steps[:per_step]],
+        "spmv_step_us": round(sum(t(m) for _, m in steps) / nsteps, 2),
+    }
+
+
+def write_ncu_records(pairs, out_path):
+    """profiles/dram_traffic.json from `workload|precision|engine|pipeline=csv`
+    pairs, stamped with the current kernel-source hash."""
+    out = {"kernel_hash": kernel_hash(), "records": {}}
+    for arg in pairs:
+        key, path = arg.split("=", 1)
+        out["records"][key] = ncu_summary(path, per_step=2 if "|f32|" in key else 1)
+    with open(out_path, "w") as f:
+        json.dump(out, f, indent=1)
+    return out
 
 
 def build_workload(cfg, rows=0):
@@ -588,10 +647,17 @@ def main():
     ap.add_argument("--rows", type=int, default=0,
                     help="with --config 4 and --profile-spmv: the banded random structure at "
                          "this many rows (same band, rows per process and ppn)")
+    ap.add_argument("--ncu-record", nargs="+", default=None, metavar="KEY=CSV",
+                    help="write profiles/dram_traffic.json from the ncu CSV logs of "
+                         "`--profile-spmv 2` runs, KEY = workload|precision|engine|pipeline; "
+                         "no GPU needed")
     ap.add_argument("--profile-spmv", type=int, default=0,
                     help="profiling mode: one apply, then this many SpMV-step launches; "
                          "prints nothing")
     args = ap.parse_args()
+    if args.ncu_record:
+        write_ncu_records(args.ncu_record, os.path.join(ROOT, "profiles", "dram_traffic.json"))
+        return
     if args.warmup < 3:
         args.warmup = 3
     reps = args.reps or DEFAULT_REPS.get(args.config, 10)
