@@ -74,10 +74,8 @@ extern "C" {
 #define NAPSPMV_MAP_TEXT (1u << 1)
 /* Strided row partition: row i belongs to process i mod n_p (the partition of
  * the paper's SuiteSparse runs, Sec. 5) instead of contiguous blocks (Eq. R).
- * A node's rows then interleave with every other node's, so the fused engine
- * (whose SpMV items wait on one node's messages) is not available for such a
- * plan: its applies return ERR_UNSUPPORTED; the phased and overlapped engines
- * serve it. */
+ * A node's rows then interleave with every other node's.  Every engine runs
+ * such plans (the staged remote pass of the overlapped engine is not used). */
 #define NAPSPMV_PARTITION_STRIDED (1u << 2)
 /* Majority mapping, the alternative the text names after Eq. U: node pair
  * (n,m) is sent by the process of n that owns the most values of E(n,m) and
@@ -104,8 +102,8 @@ extern "C" {
  * on->on step, b_{nl->l} from the owners' values), skipping the on->off
  * gather, pack, transfer and off->on hops of Algorithm NAPSpMV.  The plan and
  * its statistics are unchanged; the result has the same bits as the literal
- * exchange.  Phased and overlapped engines only (the fused engine, batches
- * and the no-allocation entry give ERR_UNSUPPORTED). */
+ * exchange.  Every engine, batches and the no-allocation entry run such
+ * plans. */
 #define NAPSPMV_COMPOSED_GATHERS (1u << 4)
 
 /* ------------------------------------------------------------- apply modes */
@@ -113,8 +111,9 @@ extern "C" {
 #define NAPSPMV_PREC_F32 1 /* FP32-stored values, FP32 products, FP64 sums   */
 
 #define NAPSPMV_ENGINE_DEFAULT 0 /* the plan's default engine               */
-#define NAPSPMV_ENGINE_FUSED 1   /* one persistent launch for all phases and
-                                    all chained applies (dataflow items)     */
+#define NAPSPMV_ENGINE_FUSED 1   /* one persistent, cooperative launch for all
+                                    phases and all chained applies, in levels
+                                    separated by grid barriers               */
 #define NAPSPMV_ENGINE_PHASED 2  /* one kernel per phase; chains of applies
                                     are captured once into a CUDA graph      */
 #define NAPSPMV_ENGINE_OVERLAP 3 /* as PHASED, with the on_process part of
@@ -130,7 +129,9 @@ extern "C" {
  * chunk, column-major, one lane per row (no shared-memory stage; the chunk's
  * columns and values are read coalesced straight from global memory).  Each
  * row is summed in its stored order, so the bits are those of vec = 1; the
- * vec field is ignored.  Phased and overlapped engines. */
+ * vec field is ignored.  The fused engine always sums rows this way; the
+ * phased and overlapped engines do by default where rows average more than
+ * 12 entries. */
 #define NAPSPMV_PIPELINE_SELL 3
 
 #define NAPSPMV_HALO_ON 1  /* overlapped engine: stage each process's receive
