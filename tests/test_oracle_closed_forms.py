@@ -194,3 +194,23 @@ def test_counts_2d5_scaled(n, n_p, ppn):
 def test_counts_config2_full():
     w = I.workload(2)
     _check(w.build(), w.n_p, w.ppn, counts_3d7(128, 8, 2))
+
+
+@pytest.mark.parametrize("n,f,g", [(16, 2, 2), (24, 2, 4), (32, 4, 2), (21, 2, 3)])
+def test_split_counts_3d7_closed_form(n, f, g):
+    """Node splitting (reading R20) on a 3D 7-point stencil whose nodes hold g whole
+    planes (f processes a plane, ppn = f g): an inner node has the two neighbouring
+    nodes as partners, so each partner gets a group of ppn / 2 processes and an
+    inner pair carries ppn / 2 pieces; the first and last node have one partner and
+    a group of all ppn processes, so the 4 pairs touching them carry ppn pieces.
+    Every piece is non-empty (a pair exchanges a whole plane), and splitting moves
+    the same values."""
+    A = I.poisson3d(n)
+    n_p, ppn = n * f, f * g
+    nodes = n_p // ppn
+    plain = O.OraclePlan(A.row_ptr, A.col, n_p, ppn).stats()
+    split = O.OraclePlan(A.row_ptr, A.col, n_p, ppn, flags=O.MAP_SPLIT).stats()
+    pairs = 2 * (nodes - 1)
+    assert plain["nap_inter_msgs"] == pairs
+    assert split["nap_inter_vals"] == plain["nap_inter_vals"] == pairs * n * n
+    assert split["nap_inter_msgs"] == (ppn // 2) * (pairs - 4) + ppn * 4
